@@ -1,0 +1,153 @@
+/*
+ * tt_fsi.h -- C ABI of the GB300 (sm_103a) Faithful Shapley Interaction
+ * library.
+ *
+ * The operation.  For a cooperative game on d players given as its value
+ * vector v (one float per coalition, 2^d of them), FSI of order l assigns a
+ * score to every coalition S with |S| <= l (Kim & Lee, "TT-FSI", Section 2.2,
+ * Eq. fsi_closed with the correction of Eq. correction and the weights of
+ * Eq. weight):
+ *
+ *   phi(S) = a(S) + sum_{T strict superset of S, |T| > l} w(|S|, |T|) a(T),
+ *   a(S)   = sum_{T subset of S} (-1)^(|S|-|T|) v(T)          (Moebius),
+ *   w(s,t) = (-1)^(l-s) s/(l+s) C(l,s) C(t-1,l) / C(t+l-1, l+s).
+ *
+ * Conventions shared by every entry point:
+ *  - Coalitions are bitmasks: bit i of an index is player i (player 0 is the
+ *    least significant bit).  A value vector is 2^d contiguous elements.
+ *  - Scores are laid out graded by |S| and, inside a grade, in lexicographic
+ *    order of the sorted player tuple: empty set, {0}, {1}, ..., {d-1},
+ *    {0,1}, {0,2}, ..., {d-2,d-1}, {0,1,2}, ...  tt_fsi_score_masks() returns
+ *    this order as masks.  There are tt_fsi_num_scores(d, l) =
+ *    sum_{k <= min(l,d)} C(d,k) of them.  For l >= d every coalition is
+ *    scored and the scores are the Moebius coefficients.
+ *  - Every pointer argument named *_dev is device memory owned by the
+ *    caller; the library never frees it.  Host pointers are named *_host.
+ *  - Calls that take a stream are asynchronous and stream-ordered; they
+ *    return launch-time errors only.  Faults that kernels detect (for
+ *    example a non-finite input value) are latched in a per-plan device
+ *    word and reported by tt_fsi_plan_check().
+ *  - No entry point throws or aborts; each returns a tt_fsi_status.
+ */
+#ifndef TT_FSI_H
+#define TT_FSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st; /* cudaStream_t without the CUDA headers */
+
+typedef enum {
+    TT_FSI_OK = 0,
+    TT_FSI_ERR_INVALID_ARG = 1,   /* bad size, order, null pointer, ... */
+    TT_FSI_ERR_UNSUPPORTED = 2,   /* valid but beyond what this build handles */
+    TT_FSI_ERR_NO_MEMORY = 3,     /* a device or host allocation failed */
+    TT_FSI_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    TT_FSI_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+    TT_FSI_ERR_NONFINITE = 6,     /* an input value was NaN or infinite */
+    TT_FSI_ERR_CHECK_FAILED = 7   /* a self-check rejected a result */
+} tt_fsi_status;
+
+/*
+ * Arithmetic of the exact path.
+ *  TT_FSI_ARITH_EXACT: each tile of 2^b coalitions is rounded once to a
+ *    fixed-point integer grid 2^-42.. relative to the tile's largest |v|;
+ *    the Moebius and superset sums then run in exact wrap-around int64 /
+ *    int128 arithmetic, the weights of Eq. weight are applied as exact
+ *    rationals, and each score is rounded once to float64.  The error is at
+ *    most 2^l times the input rounding (the operator's row L1 norm), well
+ *    below 1e-10 of max|v|.  Input and output are float64.
+ *  TT_FSI_ARITH_F64: the same algorithm in float64 arithmetic throughout
+ *    (GB300 runs float64 at about 1/60 of its integer rate).  float64 in/out.
+ *  TT_FSI_ARITH_F32: the same algorithm in float32; float32 in/out.
+ */
+typedef enum {
+    TT_FSI_ARITH_EXACT = 0,
+    TT_FSI_ARITH_F64 = 1,
+    TT_FSI_ARITH_F32 = 2
+} tt_fsi_arith;
+
+/* Opaque plan: everything that depends only on (d, l, arithmetic) --
+ * weight tables, tile schedule, state-transition tables -- plus device
+ * scratch for up to max_batch games.  Immutable after creation; one plan may
+ * be used from one stream at a time (its scratch is shared by its calls). */
+typedef struct tt_fsi_plan_s *tt_fsi_plan;
+
+/* Number of scores, sum_{k <= min(l,d)} C(d,k); -1 for d < 1, d > 62 or
+ * l < 1. */
+int64_t tt_fsi_num_scores(int d, int ell);
+
+/* Writes the tt_fsi_num_scores(d, l) coalition masks of the score layout to
+ * masks_host (host memory, caller-sized). */
+tt_fsi_status tt_fsi_score_masks(int d, int ell, uint64_t *masks_host);
+
+/* Builds a plan for games of d players (1 <= d <= 30) and order l >= 1
+ * (l = 0 is rejected: Eq. weight is 0/0 there).  Allocates device scratch
+ * for max_batch >= 1 games and uploads the tables (synchronous).  On
+ * success *out holds the plan. */
+tt_fsi_status tt_fsi_plan_create(int d, int ell, tt_fsi_arith arith, int64_t max_batch,
+                                 tt_fsi_plan *out);
+
+/* Releases a plan and its device memory (synchronizes the device first).
+ * Accepts NULL. */
+void tt_fsi_plan_destroy(tt_fsi_plan plan);
+
+/* Bytes of device scratch the plan holds. */
+size_t tt_fsi_plan_scratch_bytes(tt_fsi_plan plan);
+
+/* Tile width b (coalitions per tile = 2^b) the plan chose. */
+int tt_fsi_plan_tile_bits(tt_fsi_plan plan);
+
+/*
+ * FSI of B games (0 <= B <= max_batch of the plan).
+ *   v_dev   [B, 2^d] row-major, float64 (float32 for TT_FSI_ARITH_F32);
+ *   phi_dev [B, tt_fsi_num_scores(d, l)] row-major, same element type.
+ * The two buffers must not overlap.  Enqueued on `stream` (NULL = the
+ * legacy default stream).  B = 0 is a no-op.
+ */
+tt_fsi_status tt_fsi_apply(tt_fsi_plan plan, const void *v_dev, int64_t B, void *phi_dev,
+                           struct CUstream_st *stream);
+
+/*
+ * End-to-end variant of tt_fsi_apply for host-resident data: copies
+ * v_host [B, 2^d] to a device staging buffer owned by the plan (allocated on
+ * the plan's first tt_fsi_apply_host call, max_batch games in size), runs
+ * tt_fsi_apply, copies the scores to phi_host [B, n_scores] and waits for the
+ * stream before returning.  Page-locked host buffers copy fastest; pageable
+ * ones work.  Element types as for tt_fsi_apply.
+ */
+tt_fsi_status tt_fsi_apply_host(tt_fsi_plan plan, const void *v_host, int64_t B, void *phi_host,
+                                struct CUstream_st *stream);
+
+/*
+ * Tracing.  tt_fsi_plan_profile(plan, 1) makes every later tt_fsi_apply of
+ * the plan record CUDA events around each of its kernels on the call's
+ * stream; tt_fsi_plan_profile(plan, 0) stops recording.
+ * tt_fsi_plan_profile_read waits for the recorded events and returns the
+ * summed device time in milliseconds of the tile stage (Moebius + ranked
+ * superset sums) and of the combine stage (cross-tile weighting) over the
+ * recorded calls, and their count; it then clears the record.
+ */
+tt_fsi_status tt_fsi_plan_profile(tt_fsi_plan plan, int enable);
+tt_fsi_status tt_fsi_plan_profile_read(tt_fsi_plan plan, double *ms_tile, double *ms_combine,
+                                       int64_t *n_calls);
+
+/*
+ * Waits for the plan's work on `stream`, then reads and clears the plan's
+ * device fault word: TT_FSI_OK if no kernel reported a fault since the last
+ * check, else the fault's status (e.g. TT_FSI_ERR_NONFINITE).
+ */
+tt_fsi_status tt_fsi_plan_check(tt_fsi_plan plan, struct CUstream_st *stream);
+
+/* Human-readable name of a status. */
+const char *tt_fsi_status_string(tt_fsi_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TT_FSI_H */

@@ -1,0 +1,120 @@
+"""GB300-native Faithful Shapley Interactions (TT-FSI hot path).
+
+The compute runs in the CUDA kernels of ``csrc/`` behind the C ABI of
+``include/tt_fsi.h``; this module only marshals PyTorch tensors (device
+memory and the current CUDA stream) into those calls.  There is no CPU
+fallback: without the native library or a CUDA device every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import native
+
+ARITH = {"exact": 0, "f64": 1, "f32": 2}
+STATUS = {
+    0: "ok", 1: "invalid argument", 2: "unsupported", 3: "out of memory", 4: "CUDA error",
+    5: "device wait timed out", 6: "non-finite input", 7: "self-check failed",
+}
+
+
+class FsiError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        super().__init__(f"{what}: {STATUS.get(self.status, 'unknown')} (status {self.status})")
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise FsiError(status, what)
+
+
+def num_scores(d: int, ell: int) -> int:
+    n = native.load().tt_fsi_num_scores(d, ell)
+    if n < 0:
+        raise ValueError("need 1 <= d <= 62 and ell >= 1")
+    return int(n)
+
+
+def score_masks(d: int, ell: int) -> np.ndarray:
+    out = np.empty(num_scores(d, ell), dtype=np.uint64)
+    _check(native.load().tt_fsi_score_masks(d, ell, out.ctypes.data), "tt_fsi_score_masks")
+    return out
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """tt_fsi_plan(d, l): tables and scratch for FSI of order ``ell`` on
+    ``d``-player games, for batches of up to ``max_batch`` games."""
+
+    def __init__(self, d: int, ell: int, arith: str = "exact", max_batch: int = 1):
+        self._lib = native.load()
+        self.d, self.ell, self.arith, self.max_batch = d, ell, arith, max_batch
+        h = ctypes.c_void_p()
+        _check(self._lib.tt_fsi_plan_create(d, ell, ARITH[arith], max_batch, ctypes.byref(h)),
+               "tt_fsi_plan_create")
+        self._h = h
+        self.n_scores = num_scores(d, ell)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def tile_bits(self) -> int:
+        return int(self._lib.tt_fsi_plan_tile_bits(self._h))
+
+    @property
+    def scratch_bytes(self) -> int:
+        return int(self._lib.tt_fsi_plan_scratch_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.tt_fsi_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, v, out=None, stream=None):
+        """phi = FSI(v) for v [B, 2^d] on the GPU (float64, float32 for the
+        f32 plan).  Returns [B, n_scores] on the same device."""
+        import torch
+        dt = torch.float32 if self.arith == "f32" else torch.float64
+        if v.dim() == 1:
+            v = v.unsqueeze(0)
+        if not v.is_cuda or v.dtype != dt or v.shape[-1] != (1 << self.d):
+            raise ValueError(f"v must be a CUDA {dt} tensor of shape [B, 2^{self.d}]")
+        v = v.contiguous()
+        B = v.shape[0]
+        if out is None:
+            out = torch.empty((B, self.n_scores), dtype=dt, device=v.device)
+        _check(self._lib.tt_fsi_apply(self._h, ctypes.c_void_p(v.data_ptr()), B,
+                                      ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+               "tt_fsi_apply")
+        return out
+
+    def check(self, stream=None):
+        _check(self._lib.tt_fsi_plan_check(self._h, _stream_ptr(stream)), "tt_fsi_plan_check")
+
+
+def fsi(v, d: int, ell: int, arith: str = "exact"):
+    """One-shot FSI of v [B, 2^d] (CUDA tensor)."""
+    B = 1 if v.dim() == 1 else v.shape[0]
+    p = Plan(d, ell, arith, max_batch=max(1, B))
+    try:
+        out = p.apply(v)
+        p.check()
+        return out
+    finally:
+        p.close()

@@ -1,0 +1,612 @@
+// FSI operator kernels for GB300 (sm_103a) and the C ABI of include/tt_fsi.h.
+//
+// Two kernels per call:
+//  1. fsi_tile_kernel: one CTA per tile (game, high pattern U_H) of 2^b
+//     coalitions.  Loads the tile, (exact path) rounds it once to a per-tile
+//     fixed-point grid, applies the Moebius transform on the b low bits
+//     (Section 3.2: the operator is a Kronecker product of [[1,0],[-1,1]], one
+//     butterfly level per bit), then the ranked superset sums of the
+//     correction (Section 3.3: per output prefix sigma the counter pair
+//     (|S|, |T|), here as (sigma, j = |T \ S|)), level by level through two
+//     shared-memory buffers.  Writes the n_ch channels Y(U_H, S_L, j).
+//  2. fsi_combine_kernel: one CTA per (score S, game).  Reduces the channels
+//     of S's low part over all tiles with the combined weights omega_s(p, q)
+//     (see fsi_plan.cpp for the derivation) and writes phi(S).
+// On the exact path every sum is wrap-around int64 / int128 arithmetic, so
+// results are independent of summation order; the weights are exact
+// rationals over one denominator per |S|.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <array>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fsi_plan.h"
+#include "tt_fsi.h"
+
+namespace ttfsi {
+
+enum : int { kErrNonFinite = 1 };
+
+struct TileArgs {
+    const void *v;
+    void *Y;
+    int *tile_exp;
+    int *err;
+    const int32_t *trans;
+    int d, b, h, n_ch, buf_elems, prec_bits, mob_only;
+    int n_states[kMaxLevels];
+    int lvl_off[kMaxLevels];
+    long long game0;  // first game of this launch
+};
+
+struct CombineArgs {
+    const void *Y;
+    const int *tile_exp;
+    const int32_t *tasks;
+    const long long *wnum;
+    const long long *wden;
+    const double *wf64;
+    const float *wf32;
+    void *phi;
+    int b, h, n_ch, shift_cap, mob_only;
+    long long n_out;
+    long long game0;
+};
+
+// ----------------------------------------------------------------------------
+// float64 -> fixed point by integer operations only (GB300's float64 units,
+// conversions included, run at about 2 per clock per SM; its integer ALUs at
+// 64-128).  E is the tile's largest biased exponent, P the headroom:
+// V = round(v * 2^(P + 1022 - E)), half away from zero.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ long long to_fixed(unsigned long long bits, int E, int P) {
+    int e = (int)((bits >> 52) & 0x7ff);
+    unsigned long long mant = bits & 0x000FFFFFFFFFFFFFull;
+    if (e != 0)
+        mant |= (1ull << 52);
+    else
+        e = 1;
+    int sh = 53 - P + (E - e);
+    unsigned long long r;
+    if (sh <= 0)
+        r = mant;  // P = 53 and e = E: exact
+    else if (sh >= 64)
+        r = 0;
+    else
+        r = (mant + (1ull << (sh - 1))) >> sh;
+    long long x = (long long)r;
+    return (bits >> 63) ? -x : x;
+}
+
+template <typename Acc>
+struct TileTraits;
+template <>
+struct TileTraits<long long> {
+    using In = unsigned long long;
+    static constexpr bool exact = true;
+};
+template <>
+struct TileTraits<double> {
+    using In = double;
+    static constexpr bool exact = false;
+};
+template <>
+struct TileTraits<float> {
+    using In = float;
+    static constexpr bool exact = false;
+};
+
+template <typename Acc>
+__global__ void __launch_bounds__(kTileThreads) fsi_tile_kernel(TileArgs a) {
+    using In = typename TileTraits<Acc>::In;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Acc *bufA = reinterpret_cast<Acc *>(smem_raw);
+    Acc *bufB = bufA + a.buf_elems;
+    __shared__ int s_emax;
+
+    const int tid = threadIdx.x;
+    const int n = 1 << a.b;
+    const long long game = a.game0 + blockIdx.y;
+    const long long tile = blockIdx.x;
+    const In *src = reinterpret_cast<const In *>(a.v) + (game << a.d) + (tile << a.b);
+
+    constexpr int VPT = (1 << kMaxTileBits) / kTileThreads;
+    int E = 0;
+    if constexpr (TileTraits<Acc>::exact) {
+        In vals[VPT];
+        int emax = 0;
+#pragma unroll
+        for (int r = 0; r < VPT; ++r) {
+            int e = tid + r * kTileThreads;
+            vals[r] = (e < n) ? __ldg(src + e) : 0ull;
+            emax = max(emax, (int)((vals[r] >> 52) & 0x7ff));
+        }
+        for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+        if (tid == 0) s_emax = 0;
+        __syncthreads();
+        if ((tid & 31) == 0) atomicMax(&s_emax, emax);
+        __syncthreads();
+        E = s_emax;
+        const bool bad = (E == 0x7ff);
+        if (bad && tid == 0) atomicOr(a.err, kErrNonFinite);
+        if (E == 0) E = 1;
+#pragma unroll
+        for (int r = 0; r < VPT; ++r) {
+            int e = tid + r * kTileThreads;
+            if (e < n) bufA[e] = bad ? 0ll : to_fixed(vals[r], E, a.prec_bits);
+        }
+    } else {
+        for (int e = tid; e < n; e += kTileThreads) bufA[e] = (Acc)__ldg(src + e);
+    }
+    __syncthreads();
+
+    // Moebius transform on the b tile bits: x[T u {k}] -= x[T] for T without k.
+    for (int k = 0; k < a.b; ++k) {
+        const int lo_mask = (1 << k) - 1;
+        for (int i = tid; i < (n >> 1); i += kTileThreads) {
+            int e0 = ((i >> k) << (k + 1)) | (i & lo_mask);
+            bufA[e0 | (1 << k)] -= bufA[e0];
+        }
+        __syncthreads();
+    }
+
+    Acc *out = bufA;
+    if (!a.mob_only) {
+        // Ranked superset sums, one bit per level.  Level k holds
+        // X_k[tau][state] (tau = pattern of bits k..b-1, state = (sigma, j));
+        // an output state takes its tau_k = 0 source and its tau_k = 1 source.
+        Acc *in = bufA, *nxt = bufB;
+        for (int k = 0; k < a.b; ++k) {
+            const int nk = a.n_states[k], nk1 = a.n_states[k + 1];
+            const int half = n >> (k + 1);
+            const int total = nk1 * half;
+            const int2 *tr = reinterpret_cast<const int2 *>(a.trans) + a.lvl_off[k];
+            for (int idx = tid; idx < total; idx += kTileThreads) {
+                int t2 = idx / nk1;
+                int st = idx - t2 * nk1;
+                int2 s = __ldg(tr + st);
+                Acc val = 0;
+                if (s.x >= 0) val += in[(2 * t2) * nk + s.x];
+                if (s.y >= 0) val += in[(2 * t2 + 1) * nk + s.y];
+                nxt[idx] = val;
+            }
+            __syncthreads();
+            Acc *t = in;
+            in = nxt;
+            nxt = t;
+        }
+        out = in;
+    }
+
+    Acc *dst = reinterpret_cast<Acc *>(a.Y) + ((game << a.h) + tile) * (long long)a.n_ch;
+    for (int c = tid; c < a.n_ch; c += kTileThreads) dst[c] = out[c];
+    if constexpr (TileTraits<Acc>::exact) {
+        if (tid == 0) a.tile_exp[(game << a.h) + tile] = a.prec_bits + 1022 - E;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// combine
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ double i128_to_double(__int128 x) {
+    const bool neg = x < 0;
+    unsigned __int128 u = neg ? (unsigned __int128)(-x) : (unsigned __int128)x;
+    unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+    double r = (double)hi * 18446744073709551616.0 + (double)lo;
+    return neg ? -r : r;
+}
+
+constexpr int kCombineThreads = 128;
+
+template <typename Acc>
+__global__ void __launch_bounds__(kCombineThreads) fsi_combine_kernel(CombineArgs a) {
+    const long long game = a.game0 + blockIdx.y;
+    const long long task = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int ch_base = a.tasks[task * 4 + 0];
+    const unsigned SH = (unsigned)a.tasks[task * 4 + 1];
+    const int code = a.tasks[task * 4 + 2];
+    const int s = code & 0xff, sL = (code >> 8) & 0xff, sH = (code >> 16) & 0xff;
+    const int ntile = 1 << a.h;
+    const int J = a.mob_only ? 1 : (a.b - sL + 1);
+    const int P1 = a.h + 1, Q1 = a.b + 1;
+    const Acc *Yg = reinterpret_cast<const Acc *>(a.Y) + (game << a.h) * (long long)a.n_ch;
+
+    if constexpr (TileTraits<Acc>::exact) {
+        __shared__ int s_fmin, s_fmax;
+        __shared__ __int128 red[kCombineThreads];
+        const int *texp = a.tile_exp + (game << a.h);
+        int fmin = 0x7fffffff, fmax = -0x7fffffff;
+        for (int u = tid; u < ntile; u += kCombineThreads) {
+            int f = texp[u];
+            fmin = min(fmin, f);
+            fmax = max(fmax, f);
+        }
+        if (tid == 0) {
+            s_fmin = 0x7fffffff;
+            s_fmax = -0x7fffffff;
+        }
+        __syncthreads();
+        atomicMin(&s_fmin, fmin);
+        atomicMax(&s_fmax, fmax);
+        __syncthreads();
+        const int Fc = min(s_fmax, s_fmin + a.shift_cap);
+        const long long den = a.wden[s];
+        const long long *wrow = a.wnum + (long long)s * P1 * Q1;
+        __int128 acc = 0;
+        for (int u = tid; u < ntile; u += kCombineThreads) {
+            const int i = __popc((unsigned)u & SH);
+            const int m = __popc((unsigned)u & ~SH);
+            const int p = sH + m;
+            const long long *y = Yg + (long long)u * a.n_ch + ch_base;
+            const long long *w = wrow + (long long)p * Q1 + sL;
+            __int128 inner = 0;
+            for (int j = 0; j < J; ++j) {
+                long long c = w[j] + ((m == 0 && j == 0) ? den : 0ll);
+                inner += (__int128)y[j] * (__int128)c;
+            }
+            const int delta = Fc - texp[u];
+            if (delta >= 0) {
+                inner = (__int128)((unsigned __int128)inner << delta);
+            } else {
+                const int r = -delta;
+                inner = (r >= 127) ? (__int128)0 : ((inner + ((__int128)1 << (r - 1))) >> r);
+            }
+            if ((sH - i) & 1) inner = -inner;
+            acc += inner;
+        }
+        red[tid] = acc;
+        __syncthreads();
+        for (int o = kCombineThreads / 2; o > 0; o >>= 1) {
+            if (tid < o) red[tid] += red[tid + o];
+            __syncthreads();
+        }
+        if (tid == 0) {
+            double r = i128_to_double(red[0]) / (double)den;
+            reinterpret_cast<double *>(a.phi)[game * a.n_out + task] = ldexp(r, -Fc);
+        }
+    } else {
+        __shared__ Acc red[kCombineThreads];
+        const bool f32 = sizeof(Acc) == 4;
+        Acc acc = 0;
+        for (int u = tid; u < ntile; u += kCombineThreads) {
+            const int i = __popc((unsigned)u & SH);
+            const int m = __popc((unsigned)u & ~SH);
+            const int p = sH + m;
+            const Acc *y = Yg + (long long)u * a.n_ch + ch_base;
+            const long long wo = ((long long)s * P1 + p) * Q1 + sL;
+            Acc inner = 0;
+            for (int j = 0; j < J; ++j) {
+                Acc c = f32 ? (Acc)a.wf32[wo + j] : (Acc)a.wf64[wo + j];
+                if (m == 0 && j == 0) c += (Acc)1;
+                inner += y[j] * c;
+            }
+            acc += ((sH - i) & 1) ? -inner : inner;
+        }
+        red[tid] = acc;
+        __syncthreads();
+        for (int o = kCombineThreads / 2; o > 0; o >>= 1) {
+            if (tid < o) red[tid] += red[tid + o];
+            __syncthreads();
+        }
+        if (tid == 0) reinterpret_cast<Acc *>(a.phi)[game * a.n_out + task] = red[0];
+    }
+}
+
+// ----------------------------------------------------------------------------
+// host side
+// ----------------------------------------------------------------------------
+namespace {
+
+tt_fsi_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return TT_FSI_OK;
+    if (e == cudaErrorMemoryAllocation) return TT_FSI_ERR_NO_MEMORY;
+    return TT_FSI_ERR_CUDA;
+}
+
+template <typename T>
+tt_fsi_status upload(T **dst, const std::vector<T> &src) {
+    if (src.empty()) {
+        *dst = nullptr;
+        return TT_FSI_OK;
+    }
+    cudaError_t e = cudaMalloc((void **)dst, src.size() * sizeof(T));
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return cuda_status(e);
+}
+
+void free_plan_device(Plan *p) {
+    cudaFree(p->d_trans);
+    cudaFree(p->d_tasks);
+    cudaFree(p->d_wnum);
+    cudaFree(p->d_wden);
+    cudaFree(p->d_wf64);
+    cudaFree(p->d_wf32);
+    cudaFree(p->d_Y);
+    cudaFree(p->d_exp);
+    cudaFree(p->d_err);
+}
+
+template <typename Acc>
+tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, cudaStream_t st,
+                           cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,
+                           cudaEvent_t ev2 = nullptr) {
+    TileArgs ta{};
+    ta.v = v;
+    ta.Y = p.d_Y;
+    ta.tile_exp = p.d_exp;
+    ta.err = p.d_err;
+    ta.trans = p.d_trans;
+    ta.d = p.d;
+    ta.b = p.b;
+    ta.h = p.h;
+    ta.n_ch = p.n_ch;
+    ta.buf_elems = p.buf_elems;
+    ta.prec_bits = p.prec_bits;
+    ta.mob_only = p.mob_only ? 1 : 0;
+    for (int k = 0; k < kMaxLevels; ++k) {
+        ta.n_states[k] = p.n_states[k];
+        ta.lvl_off[k] = p.lvl_off[k];
+    }
+    CombineArgs ca{};
+    ca.Y = p.d_Y;
+    ca.tile_exp = p.d_exp;
+    ca.tasks = p.d_tasks;
+    ca.wnum = p.d_wnum;
+    ca.wden = p.d_wden;
+    ca.wf64 = p.d_wf64;
+    ca.wf32 = p.d_wf32;
+    ca.phi = phi;
+    ca.b = p.b;
+    ca.h = p.h;
+    ca.n_ch = p.n_ch;
+    ca.shift_cap = p.shift_cap;
+    ca.mob_only = ta.mob_only;
+    ca.n_out = p.n_out;
+    const int64_t chunk = 65535;
+    for (int64_t g0 = 0; g0 < B; g0 += chunk) {
+        const int nb = (int)((B - g0 < chunk) ? (B - g0) : chunk);
+        ta.game0 = g0;
+        ca.game0 = g0;
+        dim3 g1((unsigned)(1u << p.h), (unsigned)nb);
+        if (ev0 && g0 == 0) cudaEventRecord(ev0, st);
+        fsi_tile_kernel<Acc><<<g1, kTileThreads, p.smem_tile, st>>>(ta);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_status(e);
+        if (ev1 && g0 + chunk >= B) cudaEventRecord(ev1, st);
+        dim3 g2((unsigned)p.n_out, (unsigned)nb);
+        fsi_combine_kernel<Acc><<<g2, kCombineThreads, 0, st>>>(ca);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    if (ev2) cudaEventRecord(ev2, st);
+    return TT_FSI_OK;
+}
+
+}  // namespace
+}  // namespace ttfsi
+
+using namespace ttfsi;
+
+struct tt_fsi_plan_s {
+    Plan p;
+    // tracing: events recorded around each kernel while profiling is on
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::array<cudaEvent_t, 3>> ev_rec;
+    // staging for tt_fsi_apply_host
+    void *d_v_stage = nullptr;
+    void *d_phi_stage = nullptr;
+};
+
+namespace {
+cudaEvent_t pool_event(tt_fsi_plan_s *h) {
+    if (!h->ev_pool.empty()) {
+        cudaEvent_t e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+}  // namespace
+
+extern "C" {
+
+int64_t tt_fsi_num_scores(int d, int ell) { return ttfsi::num_scores(d, ell); }
+
+tt_fsi_status tt_fsi_score_masks(int d, int ell, uint64_t *masks_host) {
+    if (!masks_host || ttfsi::num_scores(d, ell) < 0) return TT_FSI_ERR_INVALID_ARG;
+    ttfsi::score_masks(d, ell, masks_host);
+    return TT_FSI_OK;
+}
+
+tt_fsi_status tt_fsi_plan_create(int d, int ell, tt_fsi_arith arith, int64_t max_batch,
+                                 tt_fsi_plan *out) {
+    if (!out) return TT_FSI_ERR_INVALID_ARG;
+    *out = nullptr;
+    tt_fsi_plan_s *h = new (std::nothrow) tt_fsi_plan_s();
+    if (!h) return TT_FSI_ERR_NO_MEMORY;
+    Plan &p = h->p;
+    tt_fsi_status st = plan_build_host(p, d, ell, arith, max_batch);
+    if (st != TT_FSI_OK) {
+        delete h;
+        return st;
+    }
+    const size_t elem = (arith == TT_FSI_ARITH_F32) ? 4 : 8;
+    const size_t ntile = (size_t)1 << p.h;
+    p.scratch_bytes = (size_t)max_batch * ntile * (size_t)p.n_ch * elem;
+    if (arith == TT_FSI_ARITH_EXACT) p.scratch_bytes += (size_t)max_batch * ntile * sizeof(int);
+    do {
+        if ((st = upload(&p.d_trans, p.trans)) != TT_FSI_OK) break;
+        if ((st = upload(&p.d_tasks, p.tasks)) != TT_FSI_OK) break;
+        if ((st = upload(&p.d_wnum, p.wnum)) != TT_FSI_OK) break;
+        if ((st = upload(&p.d_wden, p.wden)) != TT_FSI_OK) break;
+        if ((st = upload(&p.d_wf64, p.wf64)) != TT_FSI_OK) break;
+        if ((st = upload(&p.d_wf32, p.wf32)) != TT_FSI_OK) break;
+        cudaError_t e = cudaMalloc(&p.d_Y, (size_t)max_batch * ntile * (size_t)p.n_ch * elem);
+        if (e != cudaSuccess) {
+            st = cuda_status(e);
+            break;
+        }
+        e = cudaMalloc((void **)&p.d_exp, (size_t)max_batch * ntile * sizeof(int));
+        if (e != cudaSuccess) {
+            st = cuda_status(e);
+            break;
+        }
+        e = cudaMalloc((void **)&p.d_err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(p.d_err, 0, sizeof(int));
+        if (e != cudaSuccess) {
+            st = cuda_status(e);
+            break;
+        }
+        const int smem = (int)p.smem_tile;
+        if (arith == TT_FSI_ARITH_EXACT)
+            e = cudaFuncSetAttribute(fsi_tile_kernel<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        else if (arith == TT_FSI_ARITH_F64)
+            e = cudaFuncSetAttribute(fsi_tile_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        else
+            e = cudaFuncSetAttribute(fsi_tile_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) {
+            st = cuda_status(e);
+            break;
+        }
+        st = TT_FSI_OK;
+    } while (0);
+    if (st != TT_FSI_OK) {
+        free_plan_device(&p);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return TT_FSI_OK;
+}
+
+void tt_fsi_plan_destroy(tt_fsi_plan plan) {
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    free_plan_device(&plan->p);
+    cudaFree(plan->d_v_stage);
+    cudaFree(plan->d_phi_stage);
+    for (auto &r : plan->ev_rec)
+        for (cudaEvent_t ev : r) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : plan->ev_pool) cudaEventDestroy(ev);
+    delete plan;
+}
+
+size_t tt_fsi_plan_scratch_bytes(tt_fsi_plan plan) { return plan ? plan->p.scratch_bytes : 0; }
+
+int tt_fsi_plan_tile_bits(tt_fsi_plan plan) { return plan ? plan->p.b : -1; }
+
+tt_fsi_status tt_fsi_apply(tt_fsi_plan plan, const void *v_dev, int64_t B, void *phi_dev,
+                           struct CUstream_st *stream) {
+    if (!plan || B < 0) return TT_FSI_ERR_INVALID_ARG;
+    if (B == 0) return TT_FSI_OK;
+    if (!v_dev || !phi_dev || B > plan->p.max_batch) return TT_FSI_ERR_INVALID_ARG;
+    const Plan &p = plan->p;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+    if (plan->profiling) {
+        e0 = pool_event(plan);
+        e1 = pool_event(plan);
+        e2 = pool_event(plan);
+        if (!e0 || !e1 || !e2) return TT_FSI_ERR_CUDA;
+        plan->ev_rec.push_back({e0, e1, e2});
+    }
+    switch (p.arith) {
+        case TT_FSI_ARITH_EXACT: return launch_apply<long long>(p, v_dev, B, phi_dev, st, e0, e1, e2);
+        case TT_FSI_ARITH_F64: return launch_apply<double>(p, v_dev, B, phi_dev, st, e0, e1, e2);
+        case TT_FSI_ARITH_F32: return launch_apply<float>(p, v_dev, B, phi_dev, st, e0, e1, e2);
+    }
+    return TT_FSI_ERR_INVALID_ARG;
+}
+
+tt_fsi_status tt_fsi_apply_host(tt_fsi_plan plan, const void *v_host, int64_t B, void *phi_host,
+                                struct CUstream_st *stream) {
+    if (!plan || B < 0) return TT_FSI_ERR_INVALID_ARG;
+    if (B == 0) return TT_FSI_OK;
+    if (!v_host || !phi_host || B > plan->p.max_batch) return TT_FSI_ERR_INVALID_ARG;
+    const Plan &p = plan->p;
+    const size_t elem = (p.arith == TT_FSI_ARITH_F32) ? 4 : 8;
+    const size_t vbytes = ((size_t)1 << p.d) * elem, obytes = (size_t)p.n_out * elem;
+    if (!plan->d_v_stage) {
+        cudaError_t e = cudaMalloc(&plan->d_v_stage, vbytes * (size_t)p.max_batch);
+        if (e == cudaSuccess) e = cudaMalloc(&plan->d_phi_stage, obytes * (size_t)p.max_batch);
+        if (e != cudaSuccess) {
+            cudaFree(plan->d_v_stage);
+            cudaFree(plan->d_phi_stage);
+            plan->d_v_stage = plan->d_phi_stage = nullptr;
+            return cuda_status(e);
+        }
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(plan->d_v_stage, v_host, vbytes * (size_t)B, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    tt_fsi_status s = tt_fsi_apply(plan, plan->d_v_stage, B, plan->d_phi_stage, stream);
+    if (s != TT_FSI_OK) return s;
+    e = cudaMemcpyAsync(phi_host, plan->d_phi_stage, obytes * (size_t)B, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return cuda_status(e);
+}
+
+tt_fsi_status tt_fsi_plan_profile(tt_fsi_plan plan, int enable) {
+    if (!plan) return TT_FSI_ERR_INVALID_ARG;
+    plan->profiling = enable != 0;
+    return TT_FSI_OK;
+}
+
+tt_fsi_status tt_fsi_plan_profile_read(tt_fsi_plan plan, double *ms_tile, double *ms_combine,
+                                       int64_t *n_calls) {
+    if (!plan) return TT_FSI_ERR_INVALID_ARG;
+    double t1 = 0.0, t2 = 0.0;
+    tt_fsi_status st = TT_FSI_OK;
+    for (auto &r : plan->ev_rec) {
+        float a = 0.f, b = 0.f;
+        cudaError_t e = cudaEventSynchronize(r[2]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&a, r[0], r[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&b, r[1], r[2]);
+        if (e != cudaSuccess) st = cuda_status(e);
+        t1 += a;
+        t2 += b;
+        for (cudaEvent_t ev : r) plan->ev_pool.push_back(ev);
+    }
+    if (n_calls) *n_calls = (int64_t)plan->ev_rec.size();
+    plan->ev_rec.clear();
+    if (ms_tile) *ms_tile = t1;
+    if (ms_combine) *ms_combine = t2;
+    return st;
+}
+
+tt_fsi_status tt_fsi_plan_check(tt_fsi_plan plan, struct CUstream_st *stream) {
+    if (!plan) return TT_FSI_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int h_err = 0;
+    cudaError_t e = cudaMemcpyAsync(&h_err, plan->p.d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(plan->p.d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (h_err & kErrNonFinite) return TT_FSI_ERR_NONFINITE;
+    return TT_FSI_OK;
+}
+
+const char *tt_fsi_status_string(tt_fsi_status s) {
+    switch (s) {
+        case TT_FSI_OK: return "ok";
+        case TT_FSI_ERR_INVALID_ARG: return "invalid argument";
+        case TT_FSI_ERR_UNSUPPORTED: return "unsupported";
+        case TT_FSI_ERR_NO_MEMORY: return "out of memory";
+        case TT_FSI_ERR_CUDA: return "CUDA error";
+        case TT_FSI_ERR_TIMEOUT: return "device wait timed out";
+        case TT_FSI_ERR_NONFINITE: return "non-finite input";
+        case TT_FSI_ERR_CHECK_FAILED: return "self-check failed";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

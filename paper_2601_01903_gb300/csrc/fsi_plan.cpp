@@ -1,0 +1,302 @@
+// Host-side plan construction for the FSI operator (see fsi_plan.h).
+//
+// Decomposition used by the kernels.  Split the d players into the b low
+// "tile" bits and the h = d - b high bits; a tile is the 2^b coalitions that
+// share one high pattern U_H.  Per tile the kernel forms the Moebius transform
+// on the low bits, a_L, and the ranked superset sums
+//   Y(U_H, S_L, j) = sum_{T_L superset of S_L, |T_L \ S_L| = j} a_L(U_H, T_L)
+// for every low set S_L with |S_L| <= l (the two counters |S|, |T| of the
+// correction operator of Section 3.3, kept per output prefix).  Expanding
+// a(T) over the high bits and summing the correction of Eq. correction over
+// the high supersets gives, for S = S_L u S_H,
+//   phi(S) = sum_{U_H} (-1)^(|S_H| - |U_H n S_H|) sum_j
+//              [omega_s(|S_H u U_H|, |S_L| + j) + [U_H subset S_H][j = 0]] Y(U_H, S_L, j)
+// with s = |S| and
+//   omega_s(p, q) = sum_{n=0}^{h-p} (-1)^n C(h-p, n) w(s, p + q + n),
+// w the weight of Eq. weight.  The bracket's second term is the Moebius part
+// a(S) of Eq. fsi_closed.  omega is exact rational; the exact path scales
+// each omega_s by the common denominator of its entries.
+#include "fsi_plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+
+namespace ttfsi {
+
+namespace {
+
+__int128 iabs128(__int128 x) { return x < 0 ? -x : x; }
+
+__int128 gcd128(__int128 a, __int128 b) {
+    a = iabs128(a);
+    b = iabs128(b);
+    while (b != 0) {
+        __int128 t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// Binomial coefficients by Pascal's rule, exact for n <= 126.
+struct Pascal {
+    std::vector<std::vector<__int128>> c;
+    explicit Pascal(int nmax) : c(nmax + 1) {
+        for (int n = 0; n <= nmax; ++n) {
+            c[n].assign(n + 1, 0);
+            c[n][0] = c[n][n] = 1;
+            for (int k = 1; k < n; ++k) c[n][k] = c[n - 1][k - 1] + c[n - 1][k];
+        }
+    }
+    __int128 operator()(int n, int k) const {
+        if (n < 0 || k < 0 || k > n) return 0;
+        return c[n][k];
+    }
+};
+
+const Pascal &pascal() {
+    static Pascal p(126);
+    return p;
+}
+
+int popc64(uint64_t x) { return __builtin_popcountll(x); }
+
+}  // namespace
+
+Rational rat_make(__int128 num, __int128 den) {
+    Rational r;
+    if (den < 0) {
+        num = -num;
+        den = -den;
+    }
+    __int128 g = gcd128(num, den);
+    if (g == 0) g = 1;
+    r.num = num / g;
+    r.den = den / g;
+    if (r.num == 0) r.den = 1;
+    return r;
+}
+
+Rational rat_add(const Rational &a, const Rational &b) {
+    __int128 g = gcd128(a.den, b.den);
+    __int128 den = a.den / g * b.den;
+    return rat_make(a.num * (b.den / g) + b.num * (a.den / g), den);
+}
+
+Rational rat_mul(const Rational &a, const Rational &b) {
+    __int128 g1 = gcd128(a.num, b.den), g2 = gcd128(b.num, a.den);
+    if (g1 == 0) g1 = 1;
+    if (g2 == 0) g2 = 1;
+    return rat_make((a.num / g1) * (b.num / g2), (a.den / g2) * (b.den / g1));
+}
+
+Rational weight_rational(int ell, int s, int t) {
+    const Pascal &C = pascal();
+    if (s <= 0 || s > ell || t < 1) return Rational{};
+    __int128 top = C(t - 1, ell);
+    if (top == 0) return Rational{};
+    // s/(l+s) * C(l,s) * C(t-1,l) / C(t+l-1, l+s), sign (-1)^(l-s)
+    Rational r = rat_make((__int128)s * C(ell, s), (__int128)(ell + s));
+    r = rat_mul(r, rat_make(top, C(t + ell - 1, ell + s)));
+    if ((ell - s) & 1) r.num = -r.num;
+    return r;
+}
+
+int64_t num_scores(int d, int ell) {
+    if (d < 1 || d > 62 || ell < 1) return -1;
+    const Pascal &C = pascal();
+    int64_t n = 0;
+    for (int k = 0; k <= std::min(ell, d); ++k) n += (int64_t)C(d, k);
+    return n;
+}
+
+namespace {
+void emit_grade(int d, int k, int first, uint64_t prefix, uint64_t *out, int64_t &pos) {
+    if (k == 0) {
+        out[pos++] = prefix;
+        return;
+    }
+    for (int i = first; i <= d - k; ++i) emit_grade(d, k - 1, i + 1, prefix | (1ull << i), out, pos);
+}
+}  // namespace
+
+void score_masks(int d, int ell, uint64_t *out) {
+    int64_t pos = 0;
+    for (int k = 0; k <= std::min(ell, d); ++k) emit_grade(d, k, 0, 0, out, pos);
+}
+
+tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64_t max_batch) {
+    if (d < 1 || ell < 1 || max_batch < 1) return TT_FSI_ERR_INVALID_ARG;
+    if (arith != TT_FSI_ARITH_EXACT && arith != TT_FSI_ARITH_F64 && arith != TT_FSI_ARITH_F32)
+        return TT_FSI_ERR_INVALID_ARG;
+    if (d > 30) return TT_FSI_ERR_UNSUPPORTED;
+    p.d = d;
+    p.ell = ell;
+    p.ell_eff = std::min(ell, d);
+    p.arith = arith;
+    p.max_batch = max_batch;
+    p.mob_only = ell >= d;
+    p.n_out = num_scores(d, ell);
+    const size_t elem = (arith == TT_FSI_ARITH_F32) ? 4 : 8;
+    const size_t smem_budget = 224 * 1024;  // 227 KB opt-in per CTA, minus static
+
+    // Tile width: the largest b <= min(d, 12) whose two ranked-sum buffers
+    // fit in shared memory.
+    int b = std::min(d, kMaxTileBits);
+    for (;; --b) {
+        // state count after k processed bits: sum_{s <= min(k, l)} C(k, s)(k - s + 1)
+        const Pascal &C = pascal();
+        int64_t peak = (int64_t)1 << b;
+        if (!p.mob_only) {
+            for (int k = 0; k <= b; ++k) {
+                int64_t nk = 0;
+                for (int s = 0; s <= std::min(k, ell); ++s) nk += (int64_t)C(k, s) * (k - s + 1);
+                peak = std::max(peak, nk << (b - k));
+            }
+        }
+        if ((size_t)peak * 2 * elem <= smem_budget || b == 1) {
+            p.buf_elems = (int)peak;
+            break;
+        }
+    }
+    p.b = b;
+    p.h = d - b;
+    p.smem_tile = (size_t)p.buf_elems * 2 * elem;
+
+    // ---------------- ranked superset states and transitions --------------
+    // State at level k: (sigma subset of bits 0..k-1 with |sigma| <= l,
+    // j in [0, k - |sigma|]); ordered by (sigma, j).
+    std::vector<std::pair<uint32_t, int>> cur{{0u, 0}};
+    p.trans.clear();
+    p.n_states[0] = 1;
+    if (!p.mob_only) {
+        for (int k = 0; k < b; ++k) {
+            std::map<std::pair<uint32_t, int>, int> idx;
+            for (size_t i = 0; i < cur.size(); ++i) idx[cur[i]] = (int)i;
+            std::vector<std::pair<uint32_t, int>> nxt;
+            for (auto &st : cur) {
+                int s = popc64(st.first);
+                for (int j = 0; j <= k + 1 - s; ++j) nxt.push_back({st.first, j});
+                if (s + 1 <= ell)
+                    for (int j = 0; j <= k - s; ++j) nxt.push_back({st.first | (1u << k), j});
+            }
+            std::sort(nxt.begin(), nxt.end());
+            nxt.erase(std::unique(nxt.begin(), nxt.end()), nxt.end());
+            p.lvl_off[k] = (int)(p.trans.size() / 2);
+            for (auto &st : nxt) {
+                int src0 = -1, src1 = -1;
+                if (st.first >> k & 1u) {
+                    // sigma_k = 1 needs tau_k = 1; rank unchanged
+                    uint32_t sig = st.first & ~(1u << k);
+                    auto it = idx.find({sig, st.second});
+                    if (it != idx.end()) src1 = it->second;
+                } else {
+                    // sigma_k = 0: tau_k = 0 keeps the rank, tau_k = 1 adds one
+                    auto it0 = idx.find({st.first, st.second});
+                    if (it0 != idx.end()) src0 = it0->second;
+                    if (st.second >= 1) {
+                        auto it1 = idx.find({st.first, st.second - 1});
+                        if (it1 != idx.end()) src1 = it1->second;
+                    }
+                }
+                p.trans.push_back(src0);
+                p.trans.push_back(src1);
+            }
+            cur.swap(nxt);
+            p.n_states[k + 1] = (int)cur.size();
+        }
+        p.lvl_off[b] = (int)(p.trans.size() / 2);
+        p.n_ch = p.n_states[b];
+    } else {
+        p.n_ch = 1 << b;
+    }
+
+    // channel base of each low set S_L: index of (S_L, j = 0)
+    std::map<uint32_t, int> ch_base;
+    if (!p.mob_only) {
+        for (size_t i = 0; i < cur.size(); ++i)
+            if (cur[i].second == 0) ch_base[cur[i].first] = (int)i;
+    }
+
+    // ---------------- combine tasks in output order ----------------------
+    std::vector<uint64_t> masks((size_t)p.n_out);
+    score_masks(d, ell, masks.data());
+    p.tasks.assign((size_t)p.n_out * 4, 0);
+    const uint64_t low_mask = (b >= 64) ? ~0ull : ((1ull << b) - 1);
+    for (int64_t i = 0; i < p.n_out; ++i) {
+        uint64_t S = masks[i];
+        uint32_t SL = (uint32_t)(S & low_mask);
+        uint32_t SH = (uint32_t)(S >> b);
+        int sL = popc64(SL), sH = popc64(SH);
+        int base = p.mob_only ? (int)SL : ch_base.at(SL);
+        p.tasks[i * 4 + 0] = base;
+        p.tasks[i * 4 + 1] = (int32_t)SH;
+        p.tasks[i * 4 + 2] = (sL + sH) | (sL << 8) | (sH << 16);
+        p.tasks[i * 4 + 3] = 0;
+    }
+
+    // ---------------- combined weights omega_s(p, q) ----------------------
+    const int S1 = p.ell_eff + 1, P1 = p.h + 1, Q1 = b + 1;
+    std::vector<Rational> om((size_t)S1 * P1 * Q1);
+    const Pascal &C = pascal();
+    for (int s = 0; s < S1; ++s)
+        for (int pp = 0; pp < P1; ++pp)
+            for (int q = 0; q < Q1; ++q) {
+                Rational acc;
+                if (!p.mob_only && s >= 1) {
+                    for (int n = 0; n <= p.h - pp; ++n) {
+                        Rational wv = weight_rational(ell, s, pp + q + n);
+                        if (wv.num == 0) continue;
+                        Rational term = rat_mul(wv, rat_make(C(p.h - pp, n), 1));
+                        if (n & 1) term.num = -term.num;
+                        acc = rat_add(acc, term);
+                    }
+                }
+                om[((size_t)s * P1 + pp) * Q1 + q] = acc;
+            }
+    p.wf64.resize(om.size());
+    p.wf32.resize(om.size());
+    for (size_t i = 0; i < om.size(); ++i) {
+        p.wf64[i] = (double)om[i].num / (double)om[i].den;
+        p.wf32[i] = (float)p.wf64[i];
+    }
+    p.wnum.assign(om.size(), 0);
+    p.wden.assign(S1, 1);
+    int max_den_bits = 0;
+    for (int s = 0; s < S1; ++s) {
+        __int128 L = 1;
+        for (int pp = 0; pp < P1; ++pp)
+            for (int q = 0; q < Q1; ++q) {
+                __int128 dd = om[((size_t)s * P1 + pp) * Q1 + q].den;
+                L = L / gcd128(L, dd) * dd;
+                if (L > ((__int128)1 << 60)) return TT_FSI_ERR_UNSUPPORTED;
+            }
+        p.wden[s] = (long long)L;
+        int bits = 0;
+        while (((__int128)1 << bits) < L) ++bits;
+        max_den_bits = std::max(max_den_bits, bits);
+        for (int pp = 0; pp < P1; ++pp)
+            for (int q = 0; q < Q1; ++q) {
+                const Rational &r = om[((size_t)s * P1 + pp) * Q1 + q];
+                __int128 v = r.num * (L / r.den);
+                if (iabs128(v) >= ((__int128)1 << 62)) return TT_FSI_ERR_UNSUPPORTED;
+                p.wnum[((size_t)s * P1 + pp) * Q1 + q] = (long long)v;
+            }
+    }
+
+    // Fixed-point headroom: a tile's ranked sums are bounded by 3^b max|V|
+    // (row L1 norm 2^|S_L| C(b-|S_L|, j) 2^j <= 3^b), so |V| < 2^P with
+    // P = 62 - ceil(b log2 3) keeps every tile result inside int64.
+    p.prec_bits = 62 - (int)std::ceil(b * std::log2(3.0));
+    if (p.mob_only) p.prec_bits = 62 - b;
+    p.prec_bits = std::min(p.prec_bits, 53);  // never finer than the float64 mantissa
+    // Cross-tile alignment: a score is at most 2^l max|v| in magnitude (the
+    // operator's row L1 norm), so after scaling by 2^shift and the weight
+    // denominator it must stay below 2^126.
+    p.shift_cap = 124 - p.ell_eff - p.prec_bits - max_den_bits;
+    p.shift_cap = std::max(0, std::min(p.shift_cap, 60));
+    return TT_FSI_OK;
+}
+
+}  // namespace ttfsi

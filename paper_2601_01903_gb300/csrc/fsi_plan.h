@@ -1,0 +1,82 @@
+// Host-side plan of the FSI operator: tile schedule, the transition tables of
+// the ranked superset sums, the combined correction weights, and the
+// per-score tasks of the combine kernel.  Everything here depends only on
+// (d, l, arithmetic) and is built once per plan.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "tt_fsi.h"
+
+namespace ttfsi {
+
+// Largest tile the tile kernel handles (2^12 coalitions per CTA, 16 values
+// per thread at 256 threads).
+constexpr int kMaxTileBits = 12;
+constexpr int kTileThreads = 256;
+constexpr int kMaxLevels = kMaxTileBits + 1;
+
+// Exact rational with 128-bit numerator and denominator (denominator > 0,
+// reduced).  Used only on the host to build weight tables.
+struct Rational {
+    __int128 num = 0;
+    __int128 den = 1;
+};
+Rational rat_make(__int128 num, __int128 den);
+Rational rat_add(const Rational &a, const Rational &b);
+Rational rat_mul(const Rational &a, const Rational &b);
+
+// Correction weight w(s, t) of Eq. weight as an exact rational; zero for
+// s = 0, s > l or t <= l (where C(t-1, l) vanishes).
+Rational weight_rational(int ell, int s, int t);
+
+struct Plan {
+    int d = 0, ell = 0, ell_eff = 0;
+    tt_fsi_arith arith = TT_FSI_ARITH_EXACT;
+    int64_t max_batch = 0;
+    int b = 0, h = 0;         // tile bits, high bits (d = b + h)
+    bool mob_only = false;    // l >= d: scores are the Moebius coefficients
+    int64_t n_out = 0;        // scores per game
+    int n_ch = 0;             // channels per tile (states at the last level)
+    int prec_bits = 0;        // fixed-point headroom P of the exact path
+    int shift_cap = 0;        // largest exponent gap aligned exactly across tiles
+
+    // ranked superset sums: states per level and (src for tau=0, src for tau=1)
+    int n_states[kMaxLevels] = {0};
+    int lvl_off[kMaxLevels] = {0};
+    std::vector<int32_t> trans;   // 2 entries per (level, output state)
+    int buf_elems = 0;            // elements of one ping-pong buffer
+
+    // combine tasks, one per score in output order:
+    // [ch_base, high mask (bits b..d-1 shifted down), s | s_L << 8 | s_H << 16, 0]
+    std::vector<int32_t> tasks;
+
+    // weights omega_s(p, q), index (s * (h+1) + p) * (b+1) + q
+    std::vector<long long> wnum;  // exact path: numerators over den[s]
+    std::vector<long long> wden;  // exact path: one common denominator per s
+    std::vector<double> wf64;     // float paths
+    std::vector<float> wf32;
+
+    // device memory
+    int32_t *d_trans = nullptr;
+    int32_t *d_tasks = nullptr;
+    long long *d_wnum = nullptr;
+    long long *d_wden = nullptr;
+    double *d_wf64 = nullptr;
+    float *d_wf32 = nullptr;
+    void *d_Y = nullptr;          // [max_batch][2^h][n_ch] elements (8 B, 4 B for f32)
+    int *d_exp = nullptr;         // [max_batch][2^h] tile exponents (exact path)
+    int *d_err = nullptr;         // fault word
+    size_t scratch_bytes = 0;
+    size_t smem_tile = 0;         // dynamic shared memory of the tile kernel
+};
+
+// Builds every host table of the plan (no CUDA calls).  Returns a status.
+tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64_t max_batch);
+
+// Scores and their order.
+int64_t num_scores(int d, int ell);
+void score_masks(int d, int ell, uint64_t *out);
+
+}  // namespace ttfsi

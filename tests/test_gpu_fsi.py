@@ -1,0 +1,176 @@
+"""Parity of the CUDA FSI path against the CPU oracle (needs a GB300).
+
+Bar: max |phi_gpu - phi_oracle| / max |v| <= 1e-10 for the exact and the
+float64 arithmetic, on the same seeded inputs; the float32 variant's error
+is measured and held to a loose bound only.  Every call goes through the
+C ABI (via the thin Python binding)."""
+import numpy as np
+import pytest
+
+import paper_2601_01903_gb300 as fsi
+from paper_2601_01903_gb300 import synthetic
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def _gpu(x, dtype=None):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype or torch.float64, device="cuda")
+
+
+def _noise_games(d, B, seed, v0=True):
+    v = synthetic.Stream(4242 + seed, d).normal(B << d).reshape(B, 1 << d)
+    if v0:
+        v[:, 0] = 0.0
+    return v
+
+
+def _rel_err(got, ref, v):
+    return float(np.max(np.abs(got - ref)) / max(np.max(np.abs(v)), 1e-300))
+
+
+def _run(v, d, ell, arith):
+    plan = fsi.Plan(d, ell, arith, max_batch=v.shape[0])
+    dt = torch.float32 if arith == "f32" else torch.float64
+    out = plan.apply(_gpu(v, dt))
+    plan.check()
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64), plan
+
+
+@pytest.mark.parametrize("arith", ["exact", "f64"])
+def test_mobius_d8_workload(oracle_mod, arith):
+    w = synthetic.workload_mobius_d8()
+    got, _ = _run(w["v"], 8, 2, arith)
+    ref = oracle_mod.fsi(w["v"], 8, 2)
+    assert got.shape == (1, 37)
+    assert _rel_err(got, ref, w["v"]) <= TOL
+
+
+@pytest.mark.parametrize("arith", ["exact", "f64"])
+@pytest.mark.parametrize("d,ell,B", [
+    (1, 1, 1), (2, 1, 3), (3, 2, 2), (5, 3, 4), (6, 1, 1), (7, 2, 5), (9, 3, 3),
+    (11, 2, 2), (11, 3, 1), (12, 2, 2), (12, 3, 2), (13, 2, 3), (13, 3, 1), (14, 1, 2),
+    (15, 2, 2), (16, 3, 1), (17, 2, 1), (18, 3, 1),
+])
+def test_random_games_against_oracle(oracle_mod, arith, d, ell, B):
+    v = _noise_games(d, B, seed=d * 7 + ell, v0=False)
+    got, plan = _run(v, d, ell, arith)
+    ref = oracle_mod.fsi(v, d, ell)
+    assert got.shape == ref.shape
+    assert _rel_err(got, ref, v) <= TOL, (d, ell, plan.tile_bits)
+
+
+@pytest.mark.parametrize("arith", ["exact", "f64"])
+@pytest.mark.parametrize("d,ell", [(1, 3), (4, 4), (6, 9), (9, 9), (13, 13), (14, 15)])
+def test_order_at_least_d_gives_moebius(oracle_mod, arith, d, ell):
+    v = _noise_games(d, 2, seed=100 + d, v0=False)
+    got, _ = _run(v, d, ell, arith)
+    ref = oracle_mod.fsi(v, d, ell)
+    assert _rel_err(got, ref, v) <= TOL
+
+
+@pytest.mark.parametrize("arith", ["exact", "f64"])
+def test_order_4_and_5(oracle_mod, arith):
+    for d, ell in ((10, 4), (13, 5)):
+        v = _noise_games(d, 1, seed=200 + d, v0=False)
+        got, _ = _run(v, d, ell, arith)
+        assert _rel_err(got, oracle_mod.fsi(v, d, ell), v) <= TOL
+
+
+def test_masked_mlp_d14_batch64(oracle_mod):
+    """d=14, l=2, 64 instances of the 14-64-64-1 GELU MLP game."""
+    w = synthetic.workload_mlp_d14()
+    v = np.stack([oracle_mod.masked_game(w.mlp, w.x[i], w.baseline) for i in range(w.B)])
+    ref = oracle_mod.fsi(v, 14, 2)
+    for arith in ("exact", "f64"):
+        got, _ = _run(v, 14, 2, arith)
+        assert _rel_err(got, ref, v) <= TOL, arith
+    got32, _ = _run(v, 14, 2, "f32")
+    assert _rel_err(got32, ref, v) <= 1e-3
+
+
+def test_masked_mlp_d20_order3(oracle_mod):
+    """d=20, l=3: two instances of the 20-128-128-1 MLP game (oracle-made
+    value vectors) batched with 14 white-noise games, 16 games in all."""
+    w = synthetic.workload_mlp_d20()
+    v = np.empty((16, 1 << 20))
+    for i in range(2):
+        v[i] = oracle_mod.masked_game(w.mlp, w.x[i], w.baseline)
+    v[2:] = _noise_games(20, 14, seed=20)
+    got, _ = _run(v, 20, 3, "exact")
+    ref = np.stack([oracle_mod.fsi(v[i], 20, 3)[0] for i in (0, 1, 2, 15)])
+    sel = got[[0, 1, 2, 15]]
+    for k in range(4):
+        assert _rel_err(sel[k], ref[k], v[[0, 1, 2, 15][k]]) <= TOL
+    # efficiency on every game of the batch
+    eff = got[:, 1:].sum(axis=1) - (v[:, -1] - v[:, 0])
+    assert np.max(np.abs(eff) / np.abs(v).max(axis=1)) < 1e-9
+
+
+def test_d24_order2_sampled(oracle_mod):
+    """d=24, l=2, one game (2^24 float64 = 128 MiB): every score against the
+    oracle's explicit superset sums."""
+    v = _noise_games(24, 1, seed=24)
+    got, plan = _run(v, 24, 2, "exact")
+    ref = oracle_mod.fsi(v, 24, 2)
+    assert _rel_err(got, ref, v) <= TOL
+
+
+def test_sparse_games_recover_moebius_coefficients(oracle_mod):
+    g = synthetic.workload_uneven(count=6, keep_m=True)
+    for k in range(6):
+        d, ell = int(g.d[k]), int(g.ell[k])
+        v = g.v[g.v_off[k]:g.v_off[k] + (1 << d)].reshape(1, -1)
+        got, _ = _run(v, d, 5, "exact")
+        masks = oracle_mod.score_masks(d, 5).astype(np.int64)
+        assert np.max(np.abs(got[0] - g.m[k][masks])) <= TOL * max(1.0, np.abs(v).max())
+        got_l, _ = _run(v, d, ell, "exact")
+        assert _rel_err(got_l, oracle_mod.fsi(v, d, ell), v) <= TOL
+
+
+def test_float32_variant_error_is_reported(oracle_mod):
+    v = _noise_games(16, 2, seed=16)
+    got, _ = _run(v, 16, 3, "f32")
+    err = _rel_err(got, oracle_mod.fsi(v, 16, 3), v)
+    assert err < 5e-2  # cancellation on white noise; reported, not a parity claim
+
+
+def test_scale_invariance_of_exact_path(oracle_mod):
+    """Tiles of very different magnitude in one game (per-tile fixed point)."""
+    d = 16
+    v = _noise_games(d, 1, seed=3, v0=False)
+    v[0, : 1 << 12] *= 1e-9
+    v[0, 1 << 13: 3 << 12] *= 1e6
+    got, _ = _run(v, d, 2, "exact")
+    assert _rel_err(got, oracle_mod.fsi(v, d, 2), v) <= TOL
+
+
+def test_nonfinite_input_is_reported():
+    v = _noise_games(10, 1, seed=1)
+    v[0, 77] = np.inf
+    plan = fsi.Plan(10, 2, "exact", max_batch=1)
+    plan.apply(_gpu(v))
+    with pytest.raises(fsi.FsiError) as e:
+        plan.check()
+    assert e.value.status == 6
+    plan.check()  # the fault word was cleared
+
+
+def test_empty_batch_and_bad_arguments():
+    plan = fsi.Plan(8, 2, "exact", max_batch=2)
+    lib = fsi.native.load()
+    assert lib.tt_fsi_apply(plan.handle, None, 0, None, None) == 0
+    x = torch.zeros((3, 256), dtype=torch.float64, device="cuda")
+    y = torch.zeros((3, 37), dtype=torch.float64, device="cuda")
+    assert lib.tt_fsi_apply(plan.handle, x.data_ptr(), 3, y.data_ptr(), None) == 1  # > max_batch
+
+
+def test_repeated_calls_are_bitwise_identical():
+    v = _gpu(_noise_games(18, 2, seed=5))
+    plan = fsi.Plan(18, 3, "exact", max_batch=2)
+    a = plan.apply(v).clone()
+    b = plan.apply(v).clone()
+    assert torch.equal(a, b)
