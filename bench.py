@@ -1,0 +1,331 @@
+#!/usr/bin/env python3
+"""Throughput of the exact FSI hot path on GB300.
+
+Workload: d = 20 players, order l = 3, 16 games per batch (2^20 coalitions
+and 1351 scores each); the value vectors come from 16 instances of a
+random-init 20-128-128-1 GELU MLP evaluated with absent features set to 0.
+One step = tt_fsi_apply on the 16-game batch (Moebius + correction +
+assembly of every score).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--arith exact|f64|f32]
+  python bench.py --impl reference ...   # the CPU oracle on the host cores
+
+Under torchrun every rank processes its own 16-game batch (weak scaling,
+no collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import statistics
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "exact FSI coalitions/s (B·2^d/s, d=20 ℓ=3) and % HBM roofline; student inst/s"
+D, ELL, BATCH, HIDDEN = 20, 3, 16, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--arith", default="exact", choices=["exact", "f64", "f32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region (NVML through ctypes; reading only)
+# ---------------------------------------------------------------------------
+REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+           0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+           0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+           0x100: "display_clock_setting"}
+
+
+class ClockSampler:
+    def __init__(self, index: int):
+        self.samples, self.reasons = [], 0
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._nvml = None
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise OSError
+            h = ctypes.c_void_p()
+            if nv.nvmlDeviceGetHandleByIndex_v2(index, ctypes.byref(h)) != 0:
+                raise OSError
+            self._nvml, self._h = nv, h
+            mx = ctypes.c_uint()
+            if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = mx.value
+        except OSError:
+            self._nvml = None
+
+    def _run(self):
+        nv, h = self._nvml, self._h
+        clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            if nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0:
+                self.samples.append(clk.value)
+            if nv.nvmlDeviceGetCurrentClocksEventReasons(h, ctypes.byref(rs)) == 0:
+                self.reasons |= rs.value & ~0x1
+            time.sleep(0.0005)
+
+    def __enter__(self):
+        if self._nvml is not None:
+            self._t = threading.Thread(target=self._run, daemon=True)
+            self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        if self._nvml is not None:
+            self._stop.set()
+            self._t.join()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": [n for b, n in REASONS.items() if self.reasons & b],
+                "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# inputs
+# ---------------------------------------------------------------------------
+def make_inputs(device):
+    """16 value vectors of the d=20 masked-MLP workload, float64 on device."""
+    import numpy as np
+    import torch
+    from paper_2601_01903_gb300 import synthetic
+    import paper_2601_01903_gb300 as fsi
+    w = synthetic.workload_mlp_d20()
+    v = torch.empty((BATCH, 1 << D), dtype=torch.float64, device=device)
+    fsi.masked_game_into(w.mlp, torch.as_tensor(w.x, device=device),
+                         torch.as_tensor(w.baseline, device=device), v)
+    torch.cuda.synchronize(device)
+    return v, w
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_traffic():
+    """dram bytes per launch of the tile kernel from the committed ncu
+    summary, if the kernel source still matches the one profiled."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, t.get("source", ""))
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if h != t.get("source_sha256_16"):
+        return None
+    return t.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(v_host_games, budget_s=12.0):
+    """The oracle as it stands, on this host's cores, over whole games of the
+    same workload until about budget_s seconds of work."""
+    import oracle
+    import numpy as np
+    oracle.build()
+    t0 = time.perf_counter()
+    done = 0
+    for g in range(v_host_games.shape[0]):
+        oracle.fsi(v_host_games[g], D, ELL)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done * (1 << D) / dt, "unit": "coalitions/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{done} of the {BATCH} d=20 l=3 masked-MLP games, whole games "
+                      f"(closed form, explicit superset sums, OpenMP over scores)"}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    import numpy as np
+    import oracle
+    if rank != 0:
+        return
+    from paper_2601_01903_gb300 import synthetic
+    oracle.build()
+    w = synthetic.workload_mlp_d20()
+    # one whole game per step, its value vector from the oracle's masked game
+    v = oracle.masked_game(w.mlp, w.x[0], w.baseline)
+    for _ in range(args.warmup):
+        oracle.fsi(v, D, ELL)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.fsi(v, D, ELL)
+    dt = time.perf_counter() - t0
+    value = args.steps * (1 << D) / dt
+    line = {"metric": METRIC, "value": value, "unit": "coalitions/s", "impl": "reference",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "mlp_d20_l3_b16", "d": D, "ell": ELL, "global_batch": BATCH,
+                       "reference_step": "one whole game of the batch per step"},
+            "cpu_baseline": {"value": value, "unit": "coalitions/s", "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": "one d=20 l=3 masked-MLP game per step"},
+            "e2e": {"value": value, "unit": "coalitions/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import paper_2601_01903_gb300 as fsi
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    v, w = make_inputs(dev)
+    n = 1 << D
+    # Three copies of the batch rotate so that every step reads its inputs
+    # from HBM (3 x 128 MiB is larger than the 126 MiB L2).
+    copies = [v] + [v.clone() for _ in range(2)]
+    plan = fsi.Plan(D, ELL, args.arith, max_batch=BATCH)
+    phi = torch.empty((BATCH, plan.n_scores), dtype=v.dtype, device=dev)
+    if args.arith == "f32":
+        copies = [c.float() for c in copies]
+        phi = phi.float()
+    stream = torch.cuda.current_stream(dev)
+
+    def step(i):
+        plan.apply(copies[i % len(copies)], out=phi)
+
+    for i in range(args.warmup):
+        step(i)
+    plan.check()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clocks:
+        start.record(stream)
+        for i in range(args.steps):
+            step(i)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = start.elapsed_time(stop)
+    plan.check()
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * BATCH * n / (ms_per_step * 1e-3)
+
+    # per-kernel device time (tracing events on the launching stream)
+    lib = fsi.native.load()
+    lib.tt_fsi_plan_profile(plan.handle, 1)
+    nprof = min(args.steps, 100)
+    for i in range(nprof):
+        step(i)
+    lib.tt_fsi_plan_profile(plan.handle, 0)
+    t_tile, t_comb, ncalls = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    lib.tt_fsi_plan_profile_read(plan.handle, ctypes.byref(t_tile), ctypes.byref(t_comb),
+                                 ctypes.byref(ncalls))
+    tile_ms = t_tile.value / max(1, ncalls.value)
+    comb_ms = t_comb.value / max(1, ncalls.value)
+    elem = 4 if args.arith == "f32" else 8
+    alg_bytes = BATCH * n * elem  # the tile kernel's algorithmic traffic: one read of v
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (tile_ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers
+    v_host = copies[0].cpu().pin_memory()
+    phi_host = torch.empty(phi.shape, dtype=phi.dtype).pin_memory()
+    for _ in range(2):
+        lib.tt_fsi_apply_host(plan.handle, ctypes.c_void_p(v_host.data_ptr()), BATCH,
+                              ctypes.c_void_p(phi_host.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        st = lib.tt_fsi_apply_host(plan.handle, ctypes.c_void_p(v_host.data_ptr()), BATCH,
+                                   ctypes.c_void_p(phi_host.data_ptr()),
+                                   ctypes.c_void_p(stream.cuda_stream))
+        assert st == 0, st
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e = {"value": world * BATCH * n / e2e_s, "unit": "coalitions/s",
+           "h2d_bytes_per_step": BATCH * n * elem, "d2h_bytes_per_step": BATCH * plan.n_scores * elem}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "coalitions/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"exact": "int64", "f64": "f64", "f32": "f32"}[args.arith],
+        "data": "synthetic",
+        "config": {"workload": "mlp_d20_l3_b16", "d": D, "ell": ELL, "global_batch": BATCH * world,
+                   "per_gpu_batch": BATCH, "model": "masked-value MLP 20-128-128-1 GELU (random init)",
+                   "arith": args.arith, "tile_bits": plan.tile_bits,
+                   "l2": "inputs rotate over 3 copies (384 MiB > L2)", "parallelism": f"replicas{world}"},
+        "roofline": {"bound": "hbm", "kernel": "fsi_tile_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": kernel_traffic(), "tile_ms": tile_ms, "combine_ms": comb_ms,
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "clocks": clocks.summary(),
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(copies[0][:4].cpu().numpy())
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -137,6 +137,31 @@ tt_fsi_status tt_fsi_plan_profile_read(tt_fsi_plan plan, double *ms_tile, double
                                        int64_t *n_calls);
 
 /*
+ * Masked-model games.  A GELU MLP f: R^d -> R^h1 -> R^h2 -> R,
+ *   f(z) = W3 gelu(W2 gelu(W1 z + b1) + b2) + b3,  gelu(u) = u/2 (1 + erf(u/sqrt 2)),
+ * with row-major float64 device weights W1 [h1, d], W2 [h2, h1], W3 [h2] and
+ * biases b1 [h1], b2 [h2], b3 (host scalar); 1 <= d <= 30, 1 <= h1, h2 <= 256.
+ */
+typedef struct {
+    int d, h1, h2;
+    const double *W1, *b1, *W2, *b2, *W3;
+    double b3;
+} tt_fsi_mlp;
+
+/*
+ * Value vectors of the masked games of B instances (the value function of
+ * Section 2.1: the model's prediction when only the features in S are
+ * present, absent features set to the baseline):
+ *   v[b, S] = f(z),  z_i = x[b, i] if bit i of S is set, else baseline[i].
+ *   x_dev [B, d] float64, baseline_dev [d] float64, v_dev [B, 2^d] written as
+ *   float64, or float32 when out_f32 != 0 (then computed in float32, faster).
+ * Asynchronous on `stream`.
+ */
+tt_fsi_status tt_fsi_masked_game(const tt_fsi_mlp *model, const double *x_dev,
+                                 const double *baseline_dev, int64_t B, void *v_dev, int out_f32,
+                                 struct CUstream_st *stream);
+
+/*
  * Waits for the plan's work on `stream`, then reads and clears the plan's
  * device fault word: TT_FSI_OK if no kernel reported a fault since the last
  * check, else the fault's status (e.g. TT_FSI_ERR_NONFINITE).

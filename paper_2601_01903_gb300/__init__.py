@@ -118,3 +118,62 @@ def fsi(v, d: int, ell: int, arith: str = "exact"):
         return out
     finally:
         p.close()
+
+
+class _Mlp(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("h1", ctypes.c_int), ("h2", ctypes.c_int),
+                ("W1", ctypes.c_void_p), ("b1", ctypes.c_void_p), ("W2", ctypes.c_void_p),
+                ("b2", ctypes.c_void_p), ("W3", ctypes.c_void_p), ("b3", ctypes.c_double)]
+
+
+class DeviceMLP:
+    """Float64 copies of an MLP's weights on a CUDA device, in the layout of
+    tt_fsi_mlp (W1 [h1, d], W2 [h2, h1], W3 [h2], row-major)."""
+
+    def __init__(self, mlp, device="cuda"):
+        import torch
+        f = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=device)
+        self.W1, self.b1 = f(mlp.W1), f(mlp.b1)
+        self.W2, self.b2 = f(mlp.W2), f(mlp.b2)
+        self.W3 = f(np.asarray(mlp.W3).reshape(-1))
+        self.b3 = float(np.asarray(mlp.b3).reshape(-1)[0])
+        self.h1, self.d = self.W1.shape
+        self.h2 = self.W2.shape[0]
+        self._s = _Mlp(self.d, self.h1, self.h2, self.W1.data_ptr(), self.b1.data_ptr(),
+                       self.W2.data_ptr(), self.b2.data_ptr(), self.W3.data_ptr(), self.b3)
+
+    @property
+    def struct(self):
+        return self._s
+
+
+def masked_game_into(mlp, x, baseline, out, stream=None):
+    """v[b, S] = f(x[b] on S, baseline elsewhere) for all 2^d coalitions,
+    written into ``out`` ([B, 2^d], float64 or float32) by the CUDA kernel."""
+    import torch
+    dm = mlp if isinstance(mlp, DeviceMLP) else DeviceMLP(mlp, out.device)
+    x = x.to(device=out.device, dtype=torch.float64).contiguous()
+    baseline = baseline.to(device=out.device, dtype=torch.float64).contiguous()
+    if x.dim() == 1:
+        x = x.unsqueeze(0)
+    B = x.shape[0]
+    if out.shape != (B, 1 << dm.d) or not out.is_contiguous():
+        raise ValueError("out must be a contiguous [B, 2^d] tensor")
+    f32 = 1 if out.dtype == torch.float32 else 0
+    if not f32 and out.dtype != torch.float64:
+        raise ValueError("out must be float64 or float32")
+    _check(native.load().tt_fsi_masked_game(ctypes.byref(dm.struct), ctypes.c_void_p(x.data_ptr()),
+                                            ctypes.c_void_p(baseline.data_ptr()), B,
+                                            ctypes.c_void_p(out.data_ptr()), f32, _stream_ptr(stream)),
+           "tt_fsi_masked_game")
+    return out
+
+
+def masked_game(mlp, x, baseline, dtype=None, stream=None):
+    import torch
+    dm = mlp if isinstance(mlp, DeviceMLP) else DeviceMLP(mlp)
+    x = torch.as_tensor(x)
+    B = 1 if x.dim() == 1 else x.shape[0]
+    out = torch.empty((B, 1 << dm.d), dtype=dtype or torch.float64, device=dm.W1.device)
+    return masked_game_into(dm, torch.as_tensor(x, device=dm.W1.device),
+                            torch.as_tensor(baseline, device=dm.W1.device), out, stream)

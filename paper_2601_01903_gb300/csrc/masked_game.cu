@@ -1,0 +1,139 @@
+// Masked-model value function on GB300: v_x(S) = f(z), z_i = x_i for i in S
+// and baseline_i otherwise, f a GELU MLP d -> h1 -> h2 -> 1 (the value
+// function of Section 2.1, "the model's prediction when only the features in
+// S are present", with absent features replaced by a baseline).
+//
+// One CTA evaluates 2^G coalitions of one instance that share their high
+// bits.  Layer 1 is built as a subset sum: W1 z + b1 = (W1 z_high + b1) +
+// sum_{i in S_low} W1[:, i] (x_i - baseline_i), so the 2^G pre-activations of
+// a CTA cost one d-term dot product per hidden unit plus one add per
+// coalition (doubling over the G low bits).  Layer 2 is a [2^G, h1] x
+// [h1, h2] product from shared memory, layer 3 a dot product reduced across
+// the two threads that share a coalition.  The float64 instantiation is the
+// parity path; the float32 one generates training labels faster.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tt_fsi.h"
+
+namespace ttfsi_mg {
+
+constexpr int G = 6;                 // coalitions per CTA = 64
+constexpr int NC = 1 << G;
+constexpr int THREADS = 128;         // two threads per coalition in layer 2
+constexpr int MAX_H = 256;
+
+template <typename T>
+__device__ __forceinline__ T gelu(T z);
+template <>
+__device__ __forceinline__ double gelu<double>(double z) {
+    return 0.5 * z * (1.0 + erf(z * 0.70710678118654752440));
+}
+template <>
+__device__ __forceinline__ float gelu<float>(float z) {
+    return 0.5f * z * (1.0f + erff(z * 0.70710678118654752440f));
+}
+
+struct Args {
+    const double *W1, *b1, *W2, *b2, *W3;
+    double b3;
+    const double *x, *base;
+    void *v;
+    int d, h1, h2;
+    long long game0;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(THREADS) masked_game_kernel(Args a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *pre = reinterpret_cast<T *>(smem_raw);       // [NC][h1 + 1]
+    __shared__ T part[THREADS];
+    const int tid = threadIdx.x;
+    const int ld = a.h1 + 1;
+    const long long game = a.game0 + blockIdx.y;
+    const long long S_high = (long long)blockIdx.x << G;
+    const double *x = a.x + game * a.d;
+    const int g = a.d < G ? a.d : G;
+
+    // layer-1 pre-activations by subset sums over the low bits
+    for (int j = tid; j < a.h1; j += THREADS) {
+        double acc = a.b1[j];
+        for (int i = 0; i < a.d; ++i) {
+            const bool on = (i >= g) && ((S_high >> i) & 1);
+            acc += a.W1[(long long)j * a.d + i] * (on ? x[i] : a.base[i]);
+        }
+        pre[j] = (T)acc;
+        for (int k = 0; k < g; ++k) {
+            const T delta = (T)(a.W1[(long long)j * a.d + k] * (x[k] - a.base[k]));
+            for (int c = 0; c < (1 << k); ++c) pre[(c | (1 << k)) * ld + j] = pre[c * ld + j] + delta;
+        }
+    }
+    __syncthreads();
+    const int nc = 1 << g;
+    for (int idx = tid; idx < nc * a.h1; idx += THREADS) {
+        const int c = idx / a.h1, j = idx - c * a.h1;
+        pre[c * ld + j] = gelu<T>(pre[c * ld + j]);
+    }
+    __syncthreads();
+
+    // layer 2 (+ GELU) and layer 3: thread pair (c, half) covers coalition c
+    const int c = tid % NC, half = tid / NC;
+    T acc3 = 0;
+    if (c < nc) {
+        const T *row = pre + c * ld;
+        for (int j = half; j < a.h2; j += 2) {
+            const double *w = a.W2 + (long long)j * a.h1;
+            T acc = (T)a.b2[j];
+            for (int i = 0; i < a.h1; ++i) acc += (T)__ldg(w + i) * row[i];
+            acc3 += (T)a.W3[j] * gelu<T>(acc);
+        }
+    }
+    part[tid] = acc3;
+    __syncthreads();
+    if (tid < NC && tid < nc) {
+        const T val = part[tid] + part[tid + NC] + (T)a.b3;
+        reinterpret_cast<T *>(a.v)[(game << a.d) + S_high + tid] = val;
+    }
+}
+
+}  // namespace ttfsi_mg
+
+extern "C" tt_fsi_status tt_fsi_masked_game(const tt_fsi_mlp *model, const double *x_dev,
+                                           const double *baseline_dev, int64_t B, void *v_dev,
+                                           int out_f32, struct CUstream_st *stream) {
+    using namespace ttfsi_mg;
+    if (!model || B < 0) return TT_FSI_ERR_INVALID_ARG;
+    if (B == 0) return TT_FSI_OK;
+    if (!x_dev || !baseline_dev || !v_dev || !model->W1 || !model->b1 || !model->W2 || !model->b2 ||
+        !model->W3)
+        return TT_FSI_ERR_INVALID_ARG;
+    if (model->d < 1 || model->d > 30 || model->h1 < 1 || model->h2 < 1 || model->h1 > MAX_H ||
+        model->h2 > MAX_H)
+        return TT_FSI_ERR_INVALID_ARG;
+    Args a{model->W1, model->b1, model->W2, model->b2, model->W3, model->b3,
+           x_dev, baseline_dev, v_dev, model->d, model->h1, model->h2, 0};
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int g = model->d < G ? model->d : G;
+    const size_t elem = out_f32 ? sizeof(float) : sizeof(double);
+    const size_t smem = (size_t)(1 << g) * (model->h1 + 1) * elem;
+    cudaError_t e;
+    if (out_f32)
+        e = cudaFuncSetAttribute(masked_game_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else
+        e = cudaFuncSetAttribute(masked_game_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return TT_FSI_ERR_CUDA;
+    const unsigned groups = 1u << (model->d - g);
+    for (int64_t g0 = 0; g0 < B; g0 += 65535) {
+        const unsigned nb = (unsigned)((B - g0) < 65535 ? (B - g0) : 65535);
+        a.game0 = g0;
+        dim3 grid(groups, nb);
+        if (out_f32)
+            masked_game_kernel<float><<<grid, THREADS, smem, st>>>(a);
+        else
+            masked_game_kernel<double><<<grid, THREADS, smem, st>>>(a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TT_FSI_ERR_NO_MEMORY : TT_FSI_ERR_CUDA;
+    }
+    return TT_FSI_OK;
+}

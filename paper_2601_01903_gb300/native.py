@@ -129,6 +129,8 @@ def _declare(lib):
     lib.tt_fsi_plan_profile_read.restype = i
     lib.tt_fsi_plan_profile_read.argtypes = [vp, c.POINTER(c.c_double), c.POINTER(c.c_double),
                                              c.POINTER(i64)]
+    lib.tt_fsi_masked_game.restype = i
+    lib.tt_fsi_masked_game.argtypes = [vp, vp, vp, i64, vp, i, vp]
     for name, args, res in EXTRA_SIGNATURES:
         fn = getattr(lib, name, None)
         if fn is not None:
