@@ -168,6 +168,38 @@ tt_fsi_status tt_fsi_masked_game(const tt_fsi_mlp *model, const double *x_dev,
  */
 tt_fsi_status tt_fsi_plan_check(tt_fsi_plan plan, struct CUstream_st *stream);
 
+/*
+ * Allocation-free FSI, exact arithmetic.  (This entry point has no
+ * counterpart in the paper; it exists for deployment.)
+ *
+ * For callers that cannot call cudaMalloc: code that runs inside a host
+ * application or framework that owns all device memory (a fixed pool handed
+ * out by its own allocator), plug-ins and real-time services that must not
+ * allocate after start-up, and code paths where an allocation could
+ * synchronize the device or fail late.  tt_fsi_apply needs a plan, and
+ * creating a plan allocates; this call needs none.  Its scratch (the plan
+ * tables and the per-tile channels) is one file-scope device array of 64 MiB,
+ * which every GPU that loads this library holds until the process exits.
+ *
+ * Arguments as for tt_fsi_apply with an exact-arithmetic plan: v_dev
+ * [B, 2^d] float64, phi_dev [B, tt_fsi_num_scores(d, l)] float64, both
+ * caller-owned device memory.  A request whose tables and channels do not fit
+ * the 64 MiB (for example more than 10 games of d = 20, l = 3, or more than
+ * 2 games of d = 24, l = 2) returns TT_FSI_ERR_UNSUPPORTED before anything runs;
+ * split the batch.  A non-finite input value turns every score of the call
+ * into NaN (there is no plan whose fault word could report it).
+ *
+ * The first call on a device looks up the array's device address and sets
+ * the tile kernel's shared-memory limit; make that first call before any
+ * stream capture.  Each call uploads the (d, l) tables from host memory built
+ * on the first call for that (d, l).  Every call shares the one array, which
+ * keeps the last call's contents: calls that overlap on the GPU (on different
+ * streams, or from several host threads without ordering) race on it and
+ * corrupt each other's results.  Calls ordered on one stream are safe.
+ */
+tt_fsi_status tt_fsi_apply_noalloc(int d, int ell, const double *v_dev, int64_t B,
+                                   double *phi_dev, struct CUstream_st *stream);
+
 /* Human-readable name of a status. */
 const char *tt_fsi_status_string(tt_fsi_status status);
 

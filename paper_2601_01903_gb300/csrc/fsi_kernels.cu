@@ -610,3 +610,120 @@ const char *tt_fsi_status_string(tt_fsi_status s) {
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------
+// Allocation-free FSI (exact arithmetic) for callers that cannot allocate
+// device memory.  The scratch and the plan tables live in one file-scope
+// device array; nothing is allocated per call.  The array's device address is
+// taken once per device with cudaGetSymbolAddress (in host code the symbol
+// name only stands in for the array, it is not a device address).
+// ----------------------------------------------------------------------------
+#include <map>
+#include <mutex>
+
+namespace ttfsi {
+namespace {
+
+constexpr size_t kNoAllocBytes = (size_t)64 << 20;  // 64 MiB on every device that loads the library
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_na_mutex;
+unsigned char *g_na_base[kNoAllocMaxDevices] = {nullptr};
+std::map<std::pair<int, int>, Plan> g_na_plans;  // host tables per (d, l)
+
+// Writes NaN over every score when the tile kernel flagged a non-finite input.
+__global__ void noalloc_poison_kernel(const int *fault, double *phi, long long count) {
+    if (*fault == 0) return;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x)
+        phi[i] = nan;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+}  // namespace ttfsi
+
+extern "C" tt_fsi_status tt_fsi_apply_noalloc(int d, int ell, const double *v_dev, int64_t B,
+                                              double *phi_dev, struct CUstream_st *stream) {
+    using namespace ttfsi;
+    if (B < 0) return TT_FSI_ERR_INVALID_ARG;
+    if (num_scores(d, ell) < 0) return TT_FSI_ERR_INVALID_ARG;
+    if (B == 0) return TT_FSI_OK;
+    if (!v_dev || !phi_dev) return TT_FSI_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+
+    // host tables for (d, l), built once
+    auto key = std::make_pair(d, ell);
+    auto it = g_na_plans.find(key);
+    if (it == g_na_plans.end()) {
+        Plan hp;
+        tt_fsi_status s = plan_build_host(hp, d, ell, TT_FSI_ARITH_EXACT, 1);
+        if (s != TT_FSI_OK) return s;
+        it = g_na_plans.emplace(key, std::move(hp)).first;
+    }
+    Plan p = it->second;  // shallow copy of the host tables; device pointers set below
+
+    // carve the static array: fault word, tables, tile exponents, channels
+    const size_t ntile = (size_t)1 << p.h;
+    size_t off = 256;
+    const size_t o_trans = off;
+    off = align256(off + p.trans.size() * sizeof(int32_t));
+    const size_t o_tasks = off;
+    off = align256(off + p.tasks.size() * sizeof(int32_t));
+    const size_t o_wnum = off;
+    off = align256(off + p.wnum.size() * sizeof(long long));
+    const size_t o_wden = off;
+    off = align256(off + p.wden.size() * sizeof(long long));
+    const size_t o_exp = off;
+    off = align256(off + (size_t)B * ntile * sizeof(int));
+    const size_t o_Y = off;
+    off = align256(off + (size_t)B * ntile * (size_t)p.n_ch * sizeof(long long));
+    if (off > kNoAllocBytes) return TT_FSI_ERR_UNSUPPORTED;  // beyond the 64 MiB array
+
+    // once per device: the array's device address (with that device current)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TT_FSI_ERR_CUDA;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return TT_FSI_ERR_UNSUPPORTED;
+    if (!g_na_base[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return TT_FSI_ERR_CUDA;
+        if (cudaFuncSetAttribute(fsi_tile_kernel<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 224 * 1024) != cudaSuccess)
+            return TT_FSI_ERR_CUDA;
+        g_na_base[dev] = static_cast<unsigned char *>(ptr);
+    }
+    unsigned char *base = g_na_base[dev];
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+
+    // every call: clear the fault word, upload the tables, then run
+    cudaError_t e = cudaMemsetAsync(base, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + o_trans, p.trans.data(), p.trans.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + o_tasks, p.tasks.data(), p.tasks.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + o_wnum, p.wnum.data(), p.wnum.size() * sizeof(long long),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + o_wden, p.wden.data(), p.wden.size() * sizeof(long long),
+                            cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    p.d_err = reinterpret_cast<int *>(base);
+    p.d_trans = reinterpret_cast<int32_t *>(base + o_trans);
+    p.d_tasks = reinterpret_cast<int32_t *>(base + o_tasks);
+    p.d_wnum = reinterpret_cast<long long *>(base + o_wnum);
+    p.d_wden = reinterpret_cast<long long *>(base + o_wden);
+    p.d_wf64 = nullptr;
+    p.d_wf32 = nullptr;
+    p.d_exp = reinterpret_cast<int *>(base + o_exp);
+    p.d_Y = base + o_Y;
+    tt_fsi_status s = launch_apply<long long>(p, v_dev, B, phi_dev, st);
+    if (s != TT_FSI_OK) return s;
+    noalloc_poison_kernel<<<64, 256, 0, st>>>(p.d_err, phi_dev, (long long)B * p.n_out);
+    return cuda_status(cudaGetLastError());
+}

@@ -131,6 +131,8 @@ def _declare(lib):
                                              c.POINTER(i64)]
     lib.tt_fsi_masked_game.restype = i
     lib.tt_fsi_masked_game.argtypes = [vp, vp, vp, i64, vp, i, vp]
+    lib.tt_fsi_apply_noalloc.restype = i
+    lib.tt_fsi_apply_noalloc.argtypes = [i, i, vp, i64, vp, vp]
     for name, args, res in EXTRA_SIGNATURES:
         fn = getattr(lib, name, None)
         if fn is not None:
