@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <algorithm>
 #include <array>
 #include <cstring>
 #include <new>
@@ -189,6 +190,195 @@ __global__ void __launch_bounds__(kTileThreads) fsi_tile_kernel(TileArgs a) {
 }
 
 // ----------------------------------------------------------------------------
+// Fast tile kernel for b = 12, l <= 3.
+//
+// Moebius: the 16 values a thread holds always differ in 4 tile bits; three
+// register phases (bits 8-11, 4-7, 0-3) with two shared-memory transposes.
+// Shared layout of the tile: element e at e ^ ((e >> 8) & 15), which keeps
+// every half-warp on 16 distinct 8-byte bank pairs in all three phases.
+//
+// Ranked superset sums (the (|S|, |T|) counters of Section 3.3) in three
+// 4-bit blocks.  A state after k bits is (sigma, j): sigma = the output's
+// part on the processed bits (|sigma| <= l), j = |T \ S| on those bits.
+// Block 1 runs on the registers left by the last Moebius phase.  Blocks 2
+// and 3 run items (sigma, u) where u = |T| minus the popcount of the
+// untouched high bits: an item gathers its 16 inputs (one rank each,
+// j = u - |sigma| - |tau|), forms the plain superset sums over the 4 new bits
+// in registers and writes each (sigma u sigma_r, u - |sigma u sigma_r|) once,
+// so no two threads ever write the same state.
+// ----------------------------------------------------------------------------
+struct FastArgs {
+    const void *v;
+    void *Y;
+    int *tile_exp;
+    int *err;
+    const int32_t *tab;
+    int off_rec2, off_items2, off_rec3, off_items3, n_items2, n_items3;
+    int d, h, n_ch, ell, prec_bits, n4, n8, regA;
+    long long game0;
+};
+
+__device__ __forceinline__ int tile_phys(int e) { return e ^ ((e >> 8) & 15); }
+
+template <typename Acc>
+__device__ __forceinline__ void mobius16(Acc (&x)[16]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+            if (!((r >> q) & 1)) x[r | (1 << q)] -= x[r];
+}
+
+template <typename Acc>
+__device__ __forceinline__ void zeta16(Acc (&x)[16]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+            if (!((r >> q) & 1)) x[r] += x[r | (1 << q)];
+}
+
+template <typename Acc>
+__global__ void __launch_bounds__(kTileThreads) fsi_tile_fast_kernel(FastArgs a) {
+    using In = typename TileTraits<Acc>::In;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Acc *regA = reinterpret_cast<Acc *>(smem_raw);  // tile, then level-8 states
+    Acc *regB = regA + a.regA;                       // level-4 states, then channels
+    __shared__ int s_emax;
+
+    const int tid = threadIdx.x;
+    const long long game = a.game0 + blockIdx.y;
+    const long long tile = blockIdx.x;
+    const In *src = reinterpret_cast<const In *>(a.v) + (game << a.d) + (tile << 12);
+
+    Acc x[16];
+    int E = 0;
+    // ---- load (element tid + 256 r), register bits 8-11 ----
+    if constexpr (TileTraits<Acc>::exact) {
+        In raw[16];
+        int emax = 0;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            raw[r] = __ldg(src + tid + 256 * r);
+            emax = max(emax, (int)((raw[r] >> 52) & 0x7ff));
+        }
+        for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+        if (tid == 0) s_emax = 0;
+        __syncthreads();
+        if ((tid & 31) == 0) atomicMax(&s_emax, emax);
+        __syncthreads();
+        E = s_emax;
+        const bool bad = (E == 0x7ff);
+        if (bad && tid == 0) atomicOr(a.err, kErrNonFinite);
+        if (E == 0) E = 1;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) x[r] = bad ? 0ll : to_fixed(raw[r], E, a.prec_bits);
+    } else {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) x[r] = (Acc)__ldg(src + tid + 256 * r);
+    }
+    mobius16(x);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) regA[tile_phys(tid + 256 * r)] = x[r];
+    __syncthreads();
+    // ---- bits 4-7: e = (tid & 15) | r << 4 | (tid >> 4) << 8 ----
+    {
+        const int e0 = (tid & 15) | ((tid >> 4) << 8);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) x[r] = regA[tile_phys(e0 | (r << 4))];
+        mobius16(x);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) regA[tile_phys(e0 | (r << 4))] = x[r];
+    }
+    __syncthreads();
+    // ---- bits 0-3: t3 = tid & 15 (bits 8-11), t2 = tid >> 4 (bits 4-7) ----
+    const int t3 = tid & 15, t2 = tid >> 4;
+    {
+        const int e0 = (t2 << 4) | (t3 << 8);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) x[r] = regA[tile_phys(e0 | r)];
+        mobius16(x);
+    }
+    // ---- ranked block 1 (bits 0-3) from registers -> level-4 states ----
+    // level-4 index: state * 256 + (t3 + 16 * t2)
+    {
+        const int pos = t3 + 16 * t2;
+#pragma unroll
+        for (int sg = 0; sg < 16; ++sg) {
+            const int s = __popc(sg);
+            if (s > a.ell) continue;
+            const int base = __ldg(a.tab + sg);
+#pragma unroll
+            for (int j = 0; j <= 4 - s; ++j) {
+                Acc acc = 0;
+#pragma unroll
+                for (int tau = 0; tau < 16; ++tau)
+                    if ((tau & sg) == sg && __popc(tau & ~sg) == j) acc += x[tau];
+                regB[(base + j) * 256 + pos] = acc;
+            }
+        }
+    }
+    __syncthreads();
+    // ---- ranked block 2 (bits 4-7): items (sigma1, u), 16 lanes over t3 ----
+    // level-8 index: state * 16 + (t3 ^ (state & 15))
+    {
+        const int g = tid >> 4;
+        for (int it = g; it < a.n_items2; it += kTileThreads / 16) {
+            const int item = __ldg(a.tab + a.off_items2 + it);
+            const int q = item >> 8, u = item & 255;
+            const int32_t *rec = a.tab + a.off_rec2 + q * 18;
+            const int s_in = __ldg(rec), base_in = __ldg(rec + 1);
+#pragma unroll
+            for (int tau = 0; tau < 16; ++tau) {
+                const int j = u - s_in - __popc(tau);
+                x[tau] = (j >= 0 && j <= 4 - s_in) ? regB[(base_in + j) * 256 + t3 + 16 * tau] : (Acc)0;
+            }
+            zeta16(x);
+#pragma unroll
+            for (int sr = 0; sr < 16; ++sr) {
+                const int ob = __ldg(rec + 2 + sr);
+                if (ob < 0) continue;
+                const int so = s_in + __popc(sr);
+                const int j = u - so;
+                if (j < 0 || j > 8 - so) continue;
+                const int st = ob + j;
+                regA[st * 16 + (t3 ^ (st & 15))] = x[sr];
+            }
+        }
+    }
+    __syncthreads();
+    // ---- ranked block 3 (bits 8-11): one item (sigma, u) per thread ----
+    for (int it = tid; it < a.n_items3; it += kTileThreads) {
+        const int item = __ldg(a.tab + a.off_items3 + it);
+        const int q = item >> 8, u = item & 255;
+        const int32_t *rec = a.tab + a.off_rec3 + q * 18;
+        const int s_in = __ldg(rec), base_in = __ldg(rec + 1);
+#pragma unroll
+        for (int tau = 0; tau < 16; ++tau) {
+            const int j = u - s_in - __popc(tau);
+            const int st = base_in + j;
+            x[tau] = (j >= 0 && j <= 8 - s_in) ? regA[st * 16 + (tau ^ (st & 15))] : (Acc)0;
+        }
+        zeta16(x);
+#pragma unroll
+        for (int sr = 0; sr < 16; ++sr) {
+            const int ob = __ldg(rec + 2 + sr);
+            if (ob < 0) continue;
+            const int so = s_in + __popc(sr);
+            const int j = u - so;
+            if (j < 0 || j > 12 - so) continue;
+            regB[ob + j] = x[sr];
+        }
+    }
+    __syncthreads();
+    Acc *dst = reinterpret_cast<Acc *>(a.Y) + ((game << a.h) + tile) * (long long)a.n_ch;
+    for (int c = tid; c < a.n_ch; c += kTileThreads) dst[c] = regB[c];
+    if constexpr (TileTraits<Acc>::exact) {
+        if (tid == 0) a.tile_exp[(game << a.h) + tile] = a.prec_bits + 1022 - E;
+    }
+}
+
+// ----------------------------------------------------------------------------
 // combine
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ double i128_to_double(__int128 x) {
@@ -307,16 +497,26 @@ tt_fsi_status cuda_status(cudaError_t e) {
     return TT_FSI_ERR_CUDA;
 }
 
-template <typename T>
-tt_fsi_status upload(T **dst, const std::vector<T> &src) {
-    if (src.empty()) {
-        *dst = nullptr;
-        return TT_FSI_OK;
-    }
-    cudaError_t e = cudaMalloc((void **)dst, src.size() * sizeof(T));
-    if (e != cudaSuccess) return cuda_status(e);
-    e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
-    return cuda_status(e);
+// Every device-side table of a plan, so that plan creation and the
+// allocation-free entry point place the same set.
+struct TableRef {
+    void **dev;
+    const void *host;
+    size_t bytes;
+};
+
+constexpr int kPlanTables = 7;
+
+std::array<TableRef, kPlanTables> plan_tables(Plan &p) {
+    return {{
+        {(void **)&p.d_trans, p.trans.data(), p.trans.size() * sizeof(int32_t)},
+        {(void **)&p.d_tasks, p.tasks.data(), p.tasks.size() * sizeof(int32_t)},
+        {(void **)&p.d_wnum, p.wnum.data(), p.wnum.size() * sizeof(long long)},
+        {(void **)&p.d_wden, p.wden.data(), p.wden.size() * sizeof(long long)},
+        {(void **)&p.d_wf64, p.wf64.data(), p.wf64.size() * sizeof(double)},
+        {(void **)&p.d_wf32, p.wf32.data(), p.wf32.size() * sizeof(float)},
+        {(void **)&p.d_fast_tab, p.fast_tab.data(), p.fast_tab.size() * sizeof(int32_t)},
+    }};
 }
 
 void free_plan_device(Plan *p) {
@@ -329,12 +529,20 @@ void free_plan_device(Plan *p) {
     cudaFree(p->d_Y);
     cudaFree(p->d_exp);
     cudaFree(p->d_err);
+    cudaFree(p->d_fast_tab);
 }
 
 template <typename Acc>
 tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, cudaStream_t st,
                            cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,
                            cudaEvent_t ev2 = nullptr) {
+    // every table a kernel of this plan will read must be in place
+    const bool exact = TileTraits<Acc>::exact;
+    if (!p.d_tasks || !p.d_Y || !p.d_err || (p.fast12 && !p.d_fast_tab) ||
+        (!p.mob_only && !p.fast12 && !p.d_trans) ||
+        (exact && (!p.d_wnum || !p.d_wden || !p.d_exp)) ||
+        (!exact && sizeof(Acc) == 8 && !p.d_wf64) || (!exact && sizeof(Acc) == 4 && !p.d_wf32))
+        return TT_FSI_ERR_INVALID_ARG;
     TileArgs ta{};
     ta.v = v;
     ta.Y = p.d_Y;
@@ -374,7 +582,32 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
         ca.game0 = g0;
         dim3 g1((unsigned)(1u << p.h), (unsigned)nb);
         if (ev0 && g0 == 0) cudaEventRecord(ev0, st);
-        fsi_tile_kernel<Acc><<<g1, kTileThreads, p.smem_tile, st>>>(ta);
+        if (p.fast12) {
+            FastArgs fa{};
+            fa.v = v;
+            fa.Y = p.d_Y;
+            fa.tile_exp = p.d_exp;
+            fa.err = p.d_err;
+            fa.tab = p.d_fast_tab;
+            fa.off_rec2 = p.off_rec2;
+            fa.off_items2 = p.off_items2;
+            fa.off_rec3 = p.off_rec3;
+            fa.off_items3 = p.off_items3;
+            fa.n_items2 = p.n_items2;
+            fa.n_items3 = p.n_items3;
+            fa.d = p.d;
+            fa.h = p.h;
+            fa.n_ch = p.n_ch;
+            fa.ell = p.ell;
+            fa.prec_bits = p.prec_bits;
+            fa.n4 = p.n4;
+            fa.n8 = p.n8;
+            fa.regA = std::max(1 << p.b, p.n8 * 16);
+            fa.game0 = g0;
+            fsi_tile_fast_kernel<Acc><<<g1, kTileThreads, p.smem_fast, st>>>(fa);
+        } else {
+            fsi_tile_kernel<Acc><<<g1, kTileThreads, p.smem_tile, st>>>(ta);
+        }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_status(e);
         if (ev1 && g0 + chunk >= B) cudaEventRecord(ev1, st);
@@ -443,12 +676,17 @@ tt_fsi_status tt_fsi_plan_create(int d, int ell, tt_fsi_arith arith, int64_t max
     p.scratch_bytes = (size_t)max_batch * ntile * (size_t)p.n_ch * elem;
     if (arith == TT_FSI_ARITH_EXACT) p.scratch_bytes += (size_t)max_batch * ntile * sizeof(int);
     do {
-        if ((st = upload(&p.d_trans, p.trans)) != TT_FSI_OK) break;
-        if ((st = upload(&p.d_tasks, p.tasks)) != TT_FSI_OK) break;
-        if ((st = upload(&p.d_wnum, p.wnum)) != TT_FSI_OK) break;
-        if ((st = upload(&p.d_wden, p.wden)) != TT_FSI_OK) break;
-        if ((st = upload(&p.d_wf64, p.wf64)) != TT_FSI_OK) break;
-        if ((st = upload(&p.d_wf32, p.wf32)) != TT_FSI_OK) break;
+        for (const TableRef &t : plan_tables(p)) {
+            *t.dev = nullptr;
+            if (!t.bytes) continue;
+            cudaError_t e = cudaMalloc(t.dev, t.bytes);
+            if (e == cudaSuccess) e = cudaMemcpy(*t.dev, t.host, t.bytes, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                st = cuda_status(e);
+                break;
+            }
+        }
+        if (st != TT_FSI_OK) break;
         cudaError_t e = cudaMalloc(&p.d_Y, (size_t)max_batch * ntile * (size_t)p.n_ch * elem);
         if (e != cudaSuccess) {
             st = cuda_status(e);
@@ -475,6 +713,19 @@ tt_fsi_status tt_fsi_plan_create(int d, int ell, tt_fsi_arith arith, int64_t max
         if (e != cudaSuccess) {
             st = cuda_status(e);
             break;
+        }
+        if (p.fast12) {
+            const int fsm = (int)p.smem_fast;
+            if (arith == TT_FSI_ARITH_EXACT)
+                e = cudaFuncSetAttribute(fsi_tile_fast_kernel<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+            else if (arith == TT_FSI_ARITH_F64)
+                e = cudaFuncSetAttribute(fsi_tile_fast_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+            else
+                e = cudaFuncSetAttribute(fsi_tile_fast_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+            if (e != cudaSuccess) {
+                st = cuda_status(e);
+                break;
+            }
         }
         st = TT_FSI_OK;
     } while (0);
@@ -664,19 +915,17 @@ extern "C" tt_fsi_status tt_fsi_apply_noalloc(int d, int ell, const double *v_de
         if (s != TT_FSI_OK) return s;
         it = g_na_plans.emplace(key, std::move(hp)).first;
     }
-    Plan p = it->second;  // shallow copy of the host tables; device pointers set below
+    Plan &p = it->second;  // cached host tables; device pointers are set below, under the lock
 
     // carve the static array: fault word, tables, tile exponents, channels
     const size_t ntile = (size_t)1 << p.h;
     size_t off = 256;
-    const size_t o_trans = off;
-    off = align256(off + p.trans.size() * sizeof(int32_t));
-    const size_t o_tasks = off;
-    off = align256(off + p.tasks.size() * sizeof(int32_t));
-    const size_t o_wnum = off;
-    off = align256(off + p.wnum.size() * sizeof(long long));
-    const size_t o_wden = off;
-    off = align256(off + p.wden.size() * sizeof(long long));
+    std::array<TableRef, kPlanTables> tabs = plan_tables(p);
+    size_t tab_off[kPlanTables];
+    for (size_t i = 0; i < tabs.size(); ++i) {
+        tab_off[i] = off;
+        off = align256(off + tabs[i].bytes);
+    }
     const size_t o_exp = off;
     off = align256(off + (size_t)B * ntile * sizeof(int));
     const size_t o_Y = off;
@@ -691,7 +940,9 @@ extern "C" tt_fsi_status tt_fsi_apply_noalloc(int d, int ell, const double *v_de
         void *ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return TT_FSI_ERR_CUDA;
         if (cudaFuncSetAttribute(fsi_tile_kernel<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 224 * 1024) != cudaSuccess)
+                                 224 * 1024) != cudaSuccess ||
+            cudaFuncSetAttribute(fsi_tile_fast_kernel<long long>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024) != cudaSuccess)
             return TT_FSI_ERR_CUDA;
         g_na_base[dev] = static_cast<unsigned char *>(ptr);
     }
@@ -700,26 +951,13 @@ extern "C" tt_fsi_status tt_fsi_apply_noalloc(int d, int ell, const double *v_de
 
     // every call: clear the fault word, upload the tables, then run
     cudaError_t e = cudaMemsetAsync(base, 0, sizeof(int), st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(base + o_trans, p.trans.data(), p.trans.size() * sizeof(int32_t),
-                            cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(base + o_tasks, p.tasks.data(), p.tasks.size() * sizeof(int32_t),
-                            cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(base + o_wnum, p.wnum.data(), p.wnum.size() * sizeof(long long),
-                            cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(base + o_wden, p.wden.data(), p.wden.size() * sizeof(long long),
-                            cudaMemcpyHostToDevice, st);
+    for (size_t i = 0; i < tabs.size() && e == cudaSuccess; ++i) {
+        *tabs[i].dev = tabs[i].bytes ? (void *)(base + tab_off[i]) : nullptr;
+        if (tabs[i].bytes)
+            e = cudaMemcpyAsync(base + tab_off[i], tabs[i].host, tabs[i].bytes, cudaMemcpyHostToDevice, st);
+    }
     if (e != cudaSuccess) return cuda_status(e);
     p.d_err = reinterpret_cast<int *>(base);
-    p.d_trans = reinterpret_cast<int32_t *>(base + o_trans);
-    p.d_tasks = reinterpret_cast<int32_t *>(base + o_tasks);
-    p.d_wnum = reinterpret_cast<long long *>(base + o_wnum);
-    p.d_wden = reinterpret_cast<long long *>(base + o_wden);
-    p.d_wf64 = nullptr;
-    p.d_wf32 = nullptr;
     p.d_exp = reinterpret_cast<int *>(base + o_exp);
     p.d_Y = base + o_Y;
     tt_fsi_status s = launch_apply<long long>(p, v_dev, B, phi_dev, st);

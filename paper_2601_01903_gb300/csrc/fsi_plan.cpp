@@ -212,6 +212,57 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
         p.n_ch = 1 << b;
     }
 
+    // fast tile path tables (see fsi_plan.h)
+    if (!p.mob_only && b == kMaxTileBits && ell <= 3) {
+        auto states_at = [&](int k) {
+            std::vector<std::pair<uint32_t, int>> st;
+            for (uint32_t sg = 0; sg < (1u << k); ++sg) {
+                int s = popc64(sg);
+                if (s > ell) continue;
+                for (int j = 0; j <= k - s; ++j) st.push_back({sg, j});
+            }
+            std::sort(st.begin(), st.end());
+            return st;
+        };
+        auto bases = [&](const std::vector<std::pair<uint32_t, int>> &st, int k) {
+            std::vector<int> base((size_t)1 << k, -1);
+            for (size_t i = 0; i < st.size(); ++i)
+                if (st[i].second == 0) base[st[i].first] = (int)i;
+            return base;
+        };
+        auto st4 = states_at(4), st8 = states_at(8);
+        auto b4 = bases(st4, 4), b8 = bases(st8, 8), b12 = bases(cur, 12);
+        p.n4 = (int)st4.size();
+        p.n8 = (int)st8.size();
+        std::vector<int32_t> &T = p.fast_tab;
+        T.assign(b4.begin(), b4.end());
+        auto add_pass = [&](int k_in, const std::vector<int> &bin, const std::vector<int> &bout,
+                            int &off_rec, int &off_items, int &n_items) {
+            std::vector<int32_t> recs, items;
+            int q = 0;
+            for (uint32_t sg = 0; sg < (1u << k_in); ++sg) {
+                if (bin[sg] < 0) continue;
+                int s = popc64(sg);
+                recs.push_back(s);
+                recs.push_back(bin[sg]);
+                for (uint32_t sr = 0; sr < 16; ++sr) recs.push_back(bout[sg | (sr << k_in)]);
+                for (int u = s; u <= k_in + 4; ++u) items.push_back((q << 8) | u);
+                ++q;
+            }
+            off_rec = (int)T.size();
+            T.insert(T.end(), recs.begin(), recs.end());
+            off_items = (int)T.size();
+            T.insert(T.end(), items.begin(), items.end());
+            n_items = (int)items.size();
+        };
+        add_pass(4, b4, b8, p.off_rec2, p.off_items2, p.n_items2);
+        add_pass(8, b8, b12, p.off_rec3, p.off_items3, p.n_items3);
+        const size_t regA = (size_t)std::max(1 << b, p.n8 * 16);
+        const size_t regB = (size_t)std::max(p.n4 * 256, p.n_ch);
+        p.smem_fast = (regA + regB) * elem;
+        p.fast12 = p.smem_fast <= smem_budget;
+    }
+
     // channel base of each low set S_L: index of (S_L, j = 0)
     std::map<uint32_t, int> ch_base;
     if (!p.mob_only) {

@@ -48,6 +48,19 @@ struct Plan {
     std::vector<int32_t> trans;   // 2 entries per (level, output state)
     int buf_elems = 0;            // elements of one ping-pong buffer
 
+    // Fast tile path (b = 12, l <= 3): Moebius in registers, ranked sums in
+    // three 4-bit register blocks with absolute-popcount items.  Table layout
+    // (int32): base4[16] | rec2[n_rec2][18] | items2[n_items2] |
+    // rec3[n_rec3][18] | items3[n_items3]; a record is {|sigma|, base of
+    // (sigma, j=0) at its level, base of (sigma u sigma_r, 0) at the next
+    // level for each of the 16 sigma_r (-1 if pruned)}; an item is q << 8 | u.
+    bool fast12 = false;
+    std::vector<int32_t> fast_tab;
+    int off_rec2 = 0, off_items2 = 0, off_rec3 = 0, off_items3 = 0;
+    int n_items2 = 0, n_items3 = 0, n4 = 0, n8 = 0;
+    size_t smem_fast = 0;
+    int32_t *d_fast_tab = nullptr;
+
     // combine tasks, one per score in output order:
     // [ch_base, high mask (bits b..d-1 shifted down), s | s_L << 8 | s_H << 16, 0]
     std::vector<int32_t> tasks;
