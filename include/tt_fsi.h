@@ -184,8 +184,8 @@ tt_fsi_status tt_fsi_plan_check(tt_fsi_plan plan, struct CUstream_st *stream);
  * Arguments as for tt_fsi_apply with an exact-arithmetic plan: v_dev
  * [B, 2^d] float64, phi_dev [B, tt_fsi_num_scores(d, l)] float64, both
  * caller-owned device memory.  A request whose tables and channels do not fit
- * the 64 MiB (for example more than 10 games of d = 20, l = 3, or more than
- * 2 games of d = 24, l = 2) returns TT_FSI_ERR_UNSUPPORTED before anything runs;
+ * the 64 MiB (for example more than 32 games of d = 20, l = 3, or more than
+ * 9 games of d = 24, l = 2) returns TT_FSI_ERR_UNSUPPORTED before anything runs;
  * split the batch.  A non-finite input value turns every score of the call
  * into NaN (there is no plan whose fault word could report it).
  *

@@ -204,21 +204,63 @@ __global__ void __launch_bounds__(kTileThreads) fsi_tile_kernel(TileArgs a) {
 // and 3 run items (sigma, u) where u = |T| minus the popcount of the
 // untouched high bits: an item gathers its 16 inputs (one rank each,
 // j = u - |sigma| - |tau|), forms the plain superset sums over the 4 new bits
-// in registers and writes each (sigma u sigma_r, u - |sigma u sigma_r|) once,
-// so no two threads ever write the same state.
+// in registers (only those with |sigma u sigma_r| <= l) and writes each
+// (sigma u sigma_r, u - |sigma u sigma_r|) once, so no two threads ever
+// write the same state.
+//
+// Weighting: the tile, whose high pattern U_H has u_H = |U_H| set bits, forms
+// one partial score per (S_L, s, i) -- i the size of U_H n S_H that a score
+// S = S_L u S_H of size s would see --
+//   G = (-1)^(r-i) sum_j [omega_s(u_H + r - i, |S_L| + j) + [i = u_H][j = 0]] Y(S_L, j),
+// r = s - |S_L|, so that phi(S) = sum over tiles of G(S_L, s, |U_H n S_H|).
+// On the exact path G is an exact int128 (weights as integer numerators).
 // ----------------------------------------------------------------------------
 struct FastArgs {
     const void *v;
-    void *Y;
+    void *G;
     int *tile_exp;
     int *err;
     const int32_t *tab;
+    const int32_t *gtab;
+    const long long *wnum;
+    const long long *wden;
+    const double *wf64;
+    const float *wf32;
+    int n_tab, n_g;
     int off_rec2, off_items2, off_rec3, off_items3, n_items2, n_items3;
-    int d, h, n_ch, ell, prec_bits, n4, n8, regA;
+    int d, h, n_ch, ell, prec_bits, regA, regB;
     long long game0;
 };
 
+template <typename Acc>
+struct GTraits {
+    using G = Acc;
+};
+template <>
+struct GTraits<long long> {
+    using G = __int128;
+};
+
+__device__ __forceinline__ double i128_to_double(__int128 x) {
+    const bool neg = x < 0;
+    unsigned __int128 u = neg ? (unsigned __int128)(-x) : (unsigned __int128)x;
+    unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+    double r = (double)hi * 18446744073709551616.0 + (double)lo;
+    return neg ? -r : r;
+}
+
+// Full 128-bit product of two signed 64-bit integers.
+__device__ __forceinline__ __int128 mul_wide(long long a, long long b) {
+    const unsigned long long lo = (unsigned long long)a * (unsigned long long)b;
+    const long long hi = __mul64hi(a, b);
+    return (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | lo);
+}
+
 __device__ __forceinline__ int tile_phys(int e) { return e ^ ((e >> 8) & 15); }
+
+// Popcount of a 4-bit value, written out so that it folds to a constant in
+// unrolled loops.
+__host__ __device__ constexpr int cpopc(int x) { return (x & 1) + ((x >> 1) & 1) + ((x >> 2) & 1) + ((x >> 3) & 1); }
 
 template <typename Acc>
 __device__ __forceinline__ void mobius16(Acc (&x)[16]) {
@@ -229,27 +271,84 @@ __device__ __forceinline__ void mobius16(Acc (&x)[16]) {
             if (!((r >> q) & 1)) x[r | (1 << q)] -= x[r];
 }
 
-template <typename Acc>
+// Superset sums over 4 bits, correct wherever |sigma_r| <= O.  After the
+// level of bit q an entry is still needed only if it has at most O set bits
+// among bits 0..q, so the update of entry r at bit q is skipped unless r has
+// at most O set bits below q.
+template <int O, typename Acc>
 __device__ __forceinline__ void zeta16(Acc (&x)[16]) {
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int r = 0; r < 16; ++r)
-            if (!((r >> q) & 1)) x[r] += x[r | (1 << q)];
+            if (!((r >> q) & 1) && cpopc(r & ((1 << q) - 1)) <= O) x[r] += x[r | (1 << q)];
+}
+
+// Block 2 item: inputs from the level-4 states (regB), outputs to the level-8
+// states (regA).
+template <int O, typename Acc>
+__device__ __forceinline__ void block2_item(const int32_t *rec, int u, int t3, const Acc *regB, Acc *regA) {
+    const int s_in = rec[0], base_in = rec[1];
+    Acc x[16];
+    const int common = (base_in + u - s_in) * 256 + t3;
+    const int lo = u - 4, hi = u - s_in;  // valid popcounts of tau
+#pragma unroll
+    for (int tau = 0; tau < 16; ++tau) {
+        const int pc = cpopc(tau);
+        x[tau] = (pc >= lo && pc <= hi) ? regB[common + 16 * tau - 256 * pc] : (Acc)0;
+    }
+    zeta16<O>(x);
+#pragma unroll
+    for (int sr = 0; sr < 16; ++sr) {
+        if (cpopc(sr) > O) continue;
+        const int j = u - s_in - cpopc(sr);
+        if (j < 0) continue;
+        const int st = rec[2 + sr] + j;
+        regA[st * 16 + (t3 ^ (st & 15))] = x[sr];
+    }
+}
+
+// Block 3 item: inputs from the level-8 states (regA), outputs to the
+// channels (regB).
+template <int O, typename Acc>
+__device__ __forceinline__ void block3_item(const int32_t *rec, int u, const Acc *regA, Acc *regB) {
+    const int s_in = rec[0], base_in = rec[1];
+    Acc x[16];
+    const int lo = u - 8, hi = u - s_in;
+#pragma unroll
+    for (int tau = 0; tau < 16; ++tau) {
+        const int pc = cpopc(tau);
+        const int st = base_in + u - s_in - pc;
+        x[tau] = (pc >= lo && pc <= hi) ? regA[st * 16 + (tau ^ (st & 15))] : (Acc)0;
+    }
+    zeta16<O>(x);
+#pragma unroll
+    for (int sr = 0; sr < 16; ++sr) {
+        if (cpopc(sr) > O) continue;
+        const int j = u - s_in - cpopc(sr);
+        if (j < 0) continue;
+        regB[rec[2 + sr] + j] = x[sr];
+    }
 }
 
 template <typename Acc>
 __global__ void __launch_bounds__(kTileThreads) fsi_tile_fast_kernel(FastArgs a) {
     using In = typename TileTraits<Acc>::In;
+    using GT = typename GTraits<Acc>::G;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Acc *regA = reinterpret_cast<Acc *>(smem_raw);  // tile, then level-8 states
     Acc *regB = regA + a.regA;                       // level-4 states, then channels
+    int32_t *stab = reinterpret_cast<int32_t *>(regB + a.regB);
+    int32_t *sgtab = stab + a.n_tab;
     __shared__ int s_emax;
 
     const int tid = threadIdx.x;
     const long long game = a.game0 + blockIdx.y;
     const long long tile = blockIdx.x;
     const In *src = reinterpret_cast<const In *>(a.v) + (game << a.d) + (tile << 12);
+
+    for (int i = tid; i < a.n_tab; i += kTileThreads) stab[i] = __ldg(a.tab + i);
+    for (int i = tid; i < 2 * a.n_g; i += kTileThreads) sgtab[i] = __ldg(a.gtab + i);
 
     Acc x[16];
     int E = 0;
@@ -305,15 +404,15 @@ __global__ void __launch_bounds__(kTileThreads) fsi_tile_fast_kernel(FastArgs a)
         const int pos = t3 + 16 * t2;
 #pragma unroll
         for (int sg = 0; sg < 16; ++sg) {
-            const int s = __popc(sg);
+            const int s = cpopc(sg);
             if (s > a.ell) continue;
-            const int base = __ldg(a.tab + sg);
+            const int base = stab[sg];
 #pragma unroll
             for (int j = 0; j <= 4 - s; ++j) {
                 Acc acc = 0;
 #pragma unroll
                 for (int tau = 0; tau < 16; ++tau)
-                    if ((tau & sg) == sg && __popc(tau & ~sg) == j) acc += x[tau];
+                    if ((tau & sg) == sg && cpopc(tau & ~sg) == j) acc += x[tau];
                 regB[(base + j) * 256 + pos] = acc;
             }
         }
@@ -321,73 +420,154 @@ __global__ void __launch_bounds__(kTileThreads) fsi_tile_fast_kernel(FastArgs a)
     __syncthreads();
     // ---- ranked block 2 (bits 4-7): items (sigma1, u), 16 lanes over t3 ----
     // level-8 index: state * 16 + (t3 ^ (state & 15))
-    {
-        const int g = tid >> 4;
-        for (int it = g; it < a.n_items2; it += kTileThreads / 16) {
-            const int item = __ldg(a.tab + a.off_items2 + it);
-            const int q = item >> 8, u = item & 255;
-            const int32_t *rec = a.tab + a.off_rec2 + q * 18;
-            const int s_in = __ldg(rec), base_in = __ldg(rec + 1);
-#pragma unroll
-            for (int tau = 0; tau < 16; ++tau) {
-                const int j = u - s_in - __popc(tau);
-                x[tau] = (j >= 0 && j <= 4 - s_in) ? regB[(base_in + j) * 256 + t3 + 16 * tau] : (Acc)0;
-            }
-            zeta16(x);
-#pragma unroll
-            for (int sr = 0; sr < 16; ++sr) {
-                const int ob = __ldg(rec + 2 + sr);
-                if (ob < 0) continue;
-                const int so = s_in + __popc(sr);
-                const int j = u - so;
-                if (j < 0 || j > 8 - so) continue;
-                const int st = ob + j;
-                regA[st * 16 + (t3 ^ (st & 15))] = x[sr];
-            }
+    for (int it = tid >> 4; it < a.n_items2; it += kTileThreads / 16) {
+        const int item = stab[a.off_items2 + it];
+        if (item < 0) continue;
+        const int32_t *rec = stab + a.off_rec2 + (item >> 8) * 18;
+        const int u = item & 255;
+        switch (a.ell - rec[0]) {
+            case 0: block2_item<0>(rec, u, t3, regB, regA); break;
+            case 1: block2_item<1>(rec, u, t3, regB, regA); break;
+            case 2: block2_item<2>(rec, u, t3, regB, regA); break;
+            default: block2_item<3>(rec, u, t3, regB, regA); break;
         }
     }
     __syncthreads();
     // ---- ranked block 3 (bits 8-11): one item (sigma, u) per thread ----
     for (int it = tid; it < a.n_items3; it += kTileThreads) {
-        const int item = __ldg(a.tab + a.off_items3 + it);
-        const int q = item >> 8, u = item & 255;
-        const int32_t *rec = a.tab + a.off_rec3 + q * 18;
-        const int s_in = __ldg(rec), base_in = __ldg(rec + 1);
-#pragma unroll
-        for (int tau = 0; tau < 16; ++tau) {
-            const int j = u - s_in - __popc(tau);
-            const int st = base_in + j;
-            x[tau] = (j >= 0 && j <= 8 - s_in) ? regA[st * 16 + (tau ^ (st & 15))] : (Acc)0;
-        }
-        zeta16(x);
-#pragma unroll
-        for (int sr = 0; sr < 16; ++sr) {
-            const int ob = __ldg(rec + 2 + sr);
-            if (ob < 0) continue;
-            const int so = s_in + __popc(sr);
-            const int j = u - so;
-            if (j < 0 || j > 12 - so) continue;
-            regB[ob + j] = x[sr];
+        const int item = stab[a.off_items3 + it];
+        if (item < 0) continue;
+        const int32_t *rec = stab + a.off_rec3 + (item >> 8) * 18;
+        const int u = item & 255;
+        switch (a.ell - rec[0]) {
+            case 0: block3_item<0>(rec, u, regA, regB); break;
+            case 1: block3_item<1>(rec, u, regA, regB); break;
+            case 2: block3_item<2>(rec, u, regA, regB); break;
+            default: block3_item<3>(rec, u, regA, regB); break;
         }
     }
     __syncthreads();
-    Acc *dst = reinterpret_cast<Acc *>(a.Y) + ((game << a.h) + tile) * (long long)a.n_ch;
-    for (int c = tid; c < a.n_ch; c += kTileThreads) dst[c] = regB[c];
+    // ---- partial scores G(S_L, s, i) of this tile ----
+    const int uH = __popcll((unsigned long long)tile);
+    const int P1 = a.h + 1, Q1 = 13;
+    GT *gdst = reinterpret_cast<GT *>(a.G) + ((game << a.h) + tile) * (long long)a.n_g;
+    for (int g = tid; g < a.n_g; g += kTileThreads) {
+        const int cb = sgtab[2 * g], code = sgtab[2 * g + 1];
+        const int sL = code & 0xff, s = (code >> 8) & 0xff, i = code >> 16;
+        const int r = s - sL, pp = uH + r - i;
+        GT acc = 0;
+        if (i <= uH && r - i <= a.h - uH) {
+            const Acc *y = regB + cb;
+            const int J = 13 - sL;
+            if constexpr (TileTraits<Acc>::exact) {
+                const long long *w = a.wnum + ((long long)s * P1 + pp) * Q1 + sL;
+                const long long id = (i == uH) ? a.wden[s] : 0ll;
+                for (int j = 0; j < J; ++j) {
+                    const long long c = __ldg(w + j) + (j == 0 ? id : 0ll);
+                    acc += mul_wide(y[j], c);
+                }
+            } else {
+                const long long wo = ((long long)s * P1 + pp) * Q1 + sL;
+                for (int j = 0; j < J; ++j) {
+                    Acc c = (sizeof(Acc) == 4) ? (Acc)__ldg(a.wf32 + wo + j) : (Acc)__ldg(a.wf64 + wo + j);
+                    if (j == 0 && i == uH) c += (Acc)1;
+                    acc += y[j] * c;
+                }
+            }
+            if ((r - i) & 1) acc = -acc;
+        }
+        gdst[g] = acc;
+    }
     if constexpr (TileTraits<Acc>::exact) {
         if (tid == 0) a.tile_exp[(game << a.h) + tile] = a.prec_bits + 1022 - E;
     }
 }
 
 // ----------------------------------------------------------------------------
+// Combine of the fast path: phi(S) = sum over tiles of G(S_L, s, |U_H n S_H|),
+// one warp per score, lanes over tiles.  Exact path: tile partial scores are
+// aligned to a common exponent by exact left shifts and summed in
+// wrap-around int128, then divided once by the weight denominator.
+// ----------------------------------------------------------------------------
+constexpr int kCombineFastWarps = 8;
+
+struct CombineFastArgs {
+    const void *G;
+    const int *tile_exp;
+    const int32_t *tasks;
+    const long long *wden;
+    void *phi;
+    int h, n_g, shift_cap;
+    long long n_out;
+    long long game0;
+};
+
+__device__ __forceinline__ __int128 shfl_down_i128(__int128 v, int o) {
+    unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)((unsigned __int128)v >> 64);
+    lo = __shfl_down_sync(0xffffffffu, lo, o);
+    hi = __shfl_down_sync(0xffffffffu, hi, o);
+    return (__int128)(((unsigned __int128)hi << 64) | lo);
+}
+
+template <typename Acc>
+__global__ void __launch_bounds__(32 * kCombineFastWarps) fsi_combine_fast_kernel(CombineFastArgs a) {
+    using GT = typename GTraits<Acc>::G;
+    const long long game = a.game0 + blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long task = (long long)blockIdx.x * kCombineFastWarps + warp;
+    const int ntile = 1 << a.h;
+    const GT *Gg = reinterpret_cast<const GT *>(a.G) + (game << a.h) * (long long)a.n_g;
+    if constexpr (TileTraits<Acc>::exact) {
+        __shared__ int s_fmin, s_fmax;
+        const int *texp = a.tile_exp + (game << a.h);
+        int fmin = 0x7fffffff, fmax = -0x7fffffff;
+        for (int u = threadIdx.x; u < ntile; u += blockDim.x) {
+            const int f = texp[u];
+            fmin = min(fmin, f);
+            fmax = max(fmax, f);
+        }
+        if (threadIdx.x == 0) {
+            s_fmin = 0x7fffffff;
+            s_fmax = -0x7fffffff;
+        }
+        __syncthreads();
+        atomicMin(&s_fmin, fmin);
+        atomicMax(&s_fmax, fmax);
+        __syncthreads();
+        if (task >= a.n_out) return;
+        const int Fc = min(s_fmax, s_fmin + a.shift_cap);
+        const unsigned SH = (unsigned)a.tasks[task * 4 + 1];
+        const int s = a.tasks[task * 4 + 2] & 0xff;
+        const int gb = a.tasks[task * 4 + 3];
+        __int128 acc = 0;
+        for (int u = lane; u < ntile; u += 32) {
+            __int128 g = Gg[(long long)u * a.n_g + gb + __popc((unsigned)u & SH)];
+            const int delta = Fc - texp[u];
+            if (delta >= 0)
+                g = (__int128)((unsigned __int128)g << delta);
+            else
+                g = (-delta >= 127) ? (__int128)0 : ((g + ((__int128)1 << (-delta - 1))) >> (-delta));
+            acc += g;
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += shfl_down_i128(acc, o);
+        if (lane == 0) {
+            const double r = i128_to_double(acc) / (double)a.wden[s];
+            reinterpret_cast<double *>(a.phi)[game * a.n_out + task] = ldexp(r, -Fc);
+        }
+    } else {
+        if (task >= a.n_out) return;
+        const unsigned SH = (unsigned)a.tasks[task * 4 + 1];
+        const int gb = a.tasks[task * 4 + 3];
+        Acc acc = 0;
+        for (int u = lane; u < ntile; u += 32) acc += Gg[(long long)u * a.n_g + gb + __popc((unsigned)u & SH)];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) reinterpret_cast<Acc *>(a.phi)[game * a.n_out + task] = acc;
+    }
+}
+
+// ----------------------------------------------------------------------------
 // combine
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ double i128_to_double(__int128 x) {
-    const bool neg = x < 0;
-    unsigned __int128 u = neg ? (unsigned __int128)(-x) : (unsigned __int128)x;
-    unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
-    double r = (double)hi * 18446744073709551616.0 + (double)lo;
-    return neg ? -r : r;
-}
 
 constexpr int kCombineThreads = 128;
 
@@ -505,7 +685,7 @@ struct TableRef {
     size_t bytes;
 };
 
-constexpr int kPlanTables = 7;
+constexpr int kPlanTables = 8;
 
 std::array<TableRef, kPlanTables> plan_tables(Plan &p) {
     return {{
@@ -516,7 +696,20 @@ std::array<TableRef, kPlanTables> plan_tables(Plan &p) {
         {(void **)&p.d_wf64, p.wf64.data(), p.wf64.size() * sizeof(double)},
         {(void **)&p.d_wf32, p.wf32.data(), p.wf32.size() * sizeof(float)},
         {(void **)&p.d_fast_tab, p.fast_tab.data(), p.fast_tab.size() * sizeof(int32_t)},
+        {(void **)&p.d_gtab, p.gtab.data(), p.gtab.size() * sizeof(int32_t)},
     }};
+}
+
+// Bytes of per-tile output one game needs: partial scores on the fast path
+// (int128 on the exact path), channels otherwise.
+size_t tile_out_bytes_per_game(const Plan &p) {
+    const size_t ntile = (size_t)1 << p.h;
+    if (p.fast12) {
+        const size_t g = p.arith == TT_FSI_ARITH_EXACT ? 16 : (p.arith == TT_FSI_ARITH_F64 ? 8 : 4);
+        return ntile * (size_t)p.n_g * g;
+    }
+    const size_t e = (p.arith == TT_FSI_ARITH_F32) ? 4 : 8;
+    return ntile * (size_t)p.n_ch * e;
 }
 
 void free_plan_device(Plan *p) {
@@ -530,6 +723,7 @@ void free_plan_device(Plan *p) {
     cudaFree(p->d_exp);
     cudaFree(p->d_err);
     cudaFree(p->d_fast_tab);
+    cudaFree(p->d_gtab);
 }
 
 template <typename Acc>
@@ -538,7 +732,7 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
                            cudaEvent_t ev2 = nullptr) {
     // every table a kernel of this plan will read must be in place
     const bool exact = TileTraits<Acc>::exact;
-    if (!p.d_tasks || !p.d_Y || !p.d_err || (p.fast12 && !p.d_fast_tab) ||
+    if (!p.d_tasks || !p.d_Y || !p.d_err || (p.fast12 && (!p.d_fast_tab || !p.d_gtab)) ||
         (!p.mob_only && !p.fast12 && !p.d_trans) ||
         (exact && (!p.d_wnum || !p.d_wden || !p.d_exp)) ||
         (!exact && sizeof(Acc) == 8 && !p.d_wf64) || (!exact && sizeof(Acc) == 4 && !p.d_wf32))
@@ -585,10 +779,17 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
         if (p.fast12) {
             FastArgs fa{};
             fa.v = v;
-            fa.Y = p.d_Y;
+            fa.G = p.d_Y;
             fa.tile_exp = p.d_exp;
             fa.err = p.d_err;
             fa.tab = p.d_fast_tab;
+            fa.gtab = p.d_gtab;
+            fa.wnum = p.d_wnum;
+            fa.wden = p.d_wden;
+            fa.wf64 = p.d_wf64;
+            fa.wf32 = p.d_wf32;
+            fa.n_tab = (int)p.fast_tab.size();
+            fa.n_g = p.n_g;
             fa.off_rec2 = p.off_rec2;
             fa.off_items2 = p.off_items2;
             fa.off_rec3 = p.off_rec3;
@@ -600,9 +801,8 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
             fa.n_ch = p.n_ch;
             fa.ell = p.ell;
             fa.prec_bits = p.prec_bits;
-            fa.n4 = p.n4;
-            fa.n8 = p.n8;
             fa.regA = std::max(1 << p.b, p.n8 * 16);
+            fa.regB = std::max(p.n4 * 256, p.n_ch);
             fa.game0 = g0;
             fsi_tile_fast_kernel<Acc><<<g1, kTileThreads, p.smem_fast, st>>>(fa);
         } else {
@@ -611,8 +811,24 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_status(e);
         if (ev1 && g0 + chunk >= B) cudaEventRecord(ev1, st);
-        dim3 g2((unsigned)p.n_out, (unsigned)nb);
-        fsi_combine_kernel<Acc><<<g2, kCombineThreads, 0, st>>>(ca);
+        if (p.fast12) {
+            CombineFastArgs cf{};
+            cf.G = p.d_Y;
+            cf.tile_exp = p.d_exp;
+            cf.tasks = p.d_tasks;
+            cf.wden = p.d_wden;
+            cf.phi = phi;
+            cf.h = p.h;
+            cf.n_g = p.n_g;
+            cf.shift_cap = p.shift_cap;
+            cf.n_out = p.n_out;
+            cf.game0 = g0;
+            dim3 g2((unsigned)((p.n_out + kCombineFastWarps - 1) / kCombineFastWarps), (unsigned)nb);
+            fsi_combine_fast_kernel<Acc><<<g2, 32 * kCombineFastWarps, 0, st>>>(cf);
+        } else {
+            dim3 g2((unsigned)p.n_out, (unsigned)nb);
+            fsi_combine_kernel<Acc><<<g2, kCombineThreads, 0, st>>>(ca);
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_status(e);
     }
@@ -673,7 +889,7 @@ tt_fsi_status tt_fsi_plan_create(int d, int ell, tt_fsi_arith arith, int64_t max
     }
     const size_t elem = (arith == TT_FSI_ARITH_F32) ? 4 : 8;
     const size_t ntile = (size_t)1 << p.h;
-    p.scratch_bytes = (size_t)max_batch * ntile * (size_t)p.n_ch * elem;
+    p.scratch_bytes = (size_t)max_batch * tile_out_bytes_per_game(p);
     if (arith == TT_FSI_ARITH_EXACT) p.scratch_bytes += (size_t)max_batch * ntile * sizeof(int);
     do {
         for (const TableRef &t : plan_tables(p)) {
@@ -687,7 +903,7 @@ tt_fsi_status tt_fsi_plan_create(int d, int ell, tt_fsi_arith arith, int64_t max
             }
         }
         if (st != TT_FSI_OK) break;
-        cudaError_t e = cudaMalloc(&p.d_Y, (size_t)max_batch * ntile * (size_t)p.n_ch * elem);
+        cudaError_t e = cudaMalloc(&p.d_Y, (size_t)max_batch * tile_out_bytes_per_game(p));
         if (e != cudaSuccess) {
             st = cuda_status(e);
             break;
@@ -929,7 +1145,7 @@ extern "C" tt_fsi_status tt_fsi_apply_noalloc(int d, int ell, const double *v_de
     const size_t o_exp = off;
     off = align256(off + (size_t)B * ntile * sizeof(int));
     const size_t o_Y = off;
-    off = align256(off + (size_t)B * ntile * (size_t)p.n_ch * sizeof(long long));
+    off = align256(off + (size_t)B * tile_out_bytes_per_game(p));
     if (off > kNoAllocBytes) return TT_FSI_ERR_UNSUPPORTED;  // beyond the 64 MiB array
 
     // once per device: the array's device address (with that device current)

@@ -236,9 +236,14 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
         p.n8 = (int)st8.size();
         std::vector<int32_t> &T = p.fast_tab;
         T.assign(b4.begin(), b4.end());
+        // Items are grouped by |sigma| (which fixes the pruning order of the
+        // item's superset sums) and each group is padded with idle items
+        // (-1) to a multiple of `quantum`, so that all items a warp runs at
+        // once take the same code path.
         auto add_pass = [&](int k_in, const std::vector<int> &bin, const std::vector<int> &bout,
-                            int &off_rec, int &off_items, int &n_items) {
+                            int quantum, int &off_rec, int &off_items, int &n_items) {
             std::vector<int32_t> recs, items;
+            std::vector<std::vector<int32_t>> by_s(ell + 1);
             int q = 0;
             for (uint32_t sg = 0; sg < (1u << k_in); ++sg) {
                 if (bin[sg] < 0) continue;
@@ -246,8 +251,13 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
                 recs.push_back(s);
                 recs.push_back(bin[sg]);
                 for (uint32_t sr = 0; sr < 16; ++sr) recs.push_back(bout[sg | (sr << k_in)]);
-                for (int u = s; u <= k_in + 4; ++u) items.push_back((q << 8) | u);
+                for (int u = s; u <= k_in + 4; ++u) by_s[s].push_back((q << 8) | u);
                 ++q;
+            }
+            for (auto &grp : by_s) {
+                if (grp.empty()) continue;
+                items.insert(items.end(), grp.begin(), grp.end());
+                while (items.size() % quantum) items.push_back(-1);
             }
             off_rec = (int)T.size();
             T.insert(T.end(), recs.begin(), recs.end());
@@ -255,8 +265,8 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
             T.insert(T.end(), items.begin(), items.end());
             n_items = (int)items.size();
         };
-        add_pass(4, b4, b8, p.off_rec2, p.off_items2, p.n_items2);
-        add_pass(8, b8, b12, p.off_rec3, p.off_items3, p.n_items3);
+        add_pass(4, b4, b8, 2, p.off_rec2, p.off_items2, p.n_items2);
+        add_pass(8, b8, b12, 32, p.off_rec3, p.off_items3, p.n_items3);
         const size_t regA = (size_t)std::max(1 << b, p.n8 * 16);
         const size_t regB = (size_t)std::max(p.n4 * 256, p.n_ch);
         p.smem_fast = (regA + regB) * elem;
@@ -285,6 +295,31 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
         p.tasks[i * 4 + 1] = (int32_t)SH;
         p.tasks[i * 4 + 2] = (sL + sH) | (sL << 8) | (sH << 16);
         p.tasks[i * 4 + 3] = 0;
+    }
+    if (p.fast12) {
+        // partial-score entries (S_L, s, i), S_L in channel order
+        std::map<std::pair<uint32_t, int>, int> g_of;
+        p.gtab.clear();
+        for (size_t c = 0; c < cur.size(); ++c) {
+            if (cur[c].second != 0) continue;
+            const uint32_t SL = cur[c].first;
+            const int sL = popc64(SL);
+            for (int sv = sL; sv <= std::min(ell, sL + p.h); ++sv) {
+                g_of[{SL, sv}] = (int)(p.gtab.size() / 2);
+                for (int i = 0; i <= sv - sL; ++i) {
+                    p.gtab.push_back((int32_t)c);
+                    p.gtab.push_back(sL | (sv << 8) | (i << 16));
+                }
+            }
+        }
+        p.n_g = (int)(p.gtab.size() / 2);
+        for (int64_t i = 0; i < p.n_out; ++i) {
+            uint64_t S = masks[i];
+            uint32_t SL = (uint32_t)(S & low_mask);
+            p.tasks[i * 4 + 3] = g_of.at({SL, popc64(S)});
+        }
+        p.smem_fast += (p.fast_tab.size() + p.gtab.size()) * sizeof(int32_t);
+        p.fast12 = p.smem_fast <= smem_budget;
     }
 
     // ---------------- combined weights omega_s(p, q) ----------------------

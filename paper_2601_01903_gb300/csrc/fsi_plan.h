@@ -60,6 +60,12 @@ struct Plan {
     int n_items2 = 0, n_items3 = 0, n4 = 0, n8 = 0;
     size_t smem_fast = 0;
     int32_t *d_fast_tab = nullptr;
+    // Partial scores per tile on the fast path: one entry per (S_L, s, i)
+    // (low set, |S|, |U_H n S_H|), gtab = {ch_base, s_L | s << 8 | i << 16}.
+    // The combine tasks' 4th field is the entry of (S_L, s, i = 0).
+    std::vector<int32_t> gtab;
+    int n_g = 0;
+    int32_t *d_gtab = nullptr;
 
     // combine tasks, one per score in output order:
     // [ch_base, high mask (bits b..d-1 shifted down), s | s_L << 8 | s_H << 16, 0]

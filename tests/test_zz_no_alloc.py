@@ -23,8 +23,8 @@ def _games(d, B, seed):
 def test_oversized_requests_are_rejected_before_running():
     lib = native.load()
     dummy = ctypes.c_void_p(256)  # never dereferenced: the size check comes first
-    assert lib.tt_fsi_apply_noalloc(20, 3, dummy, 11, dummy, None) == 2  # 11 games > 64 MiB
-    assert lib.tt_fsi_apply_noalloc(24, 2, dummy, 3, dummy, None) == 2
+    assert lib.tt_fsi_apply_noalloc(20, 3, dummy, 33, dummy, None) == 2  # 33 games > 64 MiB
+    assert lib.tt_fsi_apply_noalloc(24, 2, dummy, 10, dummy, None) == 2
     assert lib.tt_fsi_apply_noalloc(20, 0, dummy, 1, dummy, None) == 1  # l = 0
     assert lib.tt_fsi_apply_noalloc(20, 3, None, 1, dummy, None) == 1
     assert lib.tt_fsi_apply_noalloc(20, 3, dummy, 0, dummy, None) == 0   # empty batch
