@@ -137,6 +137,58 @@ tt_fsi_status tt_fsi_plan_profile_read(tt_fsi_plan plan, double *ms_tile, double
                                        int64_t *n_calls);
 
 /*
+ * Batches of uneven games.  Game g has d players and order l and lives at
+ * element offset v_offset of the batch's value buffer (2^d elements) and at
+ * element offset phi_offset of its score buffer (tt_fsi_num_scores(d, l)
+ * elements); games must not overlap in phi.
+ */
+typedef struct {
+    int d, ell;
+    int64_t v_offset, phi_offset;
+} tt_fsi_game;
+
+typedef struct tt_fsi_batch_s *tt_fsi_batch;
+
+/* Builds the plans (one per distinct (d, l)), the work list and the scratch
+ * of a batch (synchronous).  1 <= d <= 30, l >= 1 per game. */
+tt_fsi_status tt_fsi_batch_create(const tt_fsi_game *games_host, int64_t n_games, tt_fsi_arith arith,
+                                  tt_fsi_batch *out);
+void tt_fsi_batch_destroy(tt_fsi_batch batch);
+
+/*
+ * FSI of every game of the batch.  Games with l <= 3 and l < d run in ONE
+ * persistent launch (one CTA per SM pulling tiles, then score chunks, from a
+ * device work queue; a chunk waits for its game's tiles with a bounded
+ * number of polls and reports TT_FSI_ERR_TIMEOUT through
+ * tt_fsi_batch_check if the limit is reached).  Other games run one plan
+ * call each after it.  Element types as for tt_fsi_apply.
+ */
+tt_fsi_status tt_fsi_batch_apply(tt_fsi_batch batch, const void *v_dev, void *phi_dev,
+                                 struct CUstream_st *stream);
+/* The same results with one tt_fsi_apply per game (two launches each). */
+tt_fsi_status tt_fsi_batch_apply_per_game(tt_fsi_batch batch, const void *v_dev, void *phi_dev,
+                                          struct CUstream_st *stream);
+/* The per-game launches, captured once into a CUDA graph (per v/phi pair)
+ * and replayed. */
+tt_fsi_status tt_fsi_batch_apply_graph(tt_fsi_batch batch, const void *v_dev, void *phi_dev,
+                                       struct CUstream_st *stream);
+/* Autotuner: times the persistent launch on these buffers for tiles per work
+ * item in {1, 2, 4, 8} and scores per work item in {16, 64, 256}, keeps the
+ * fastest and returns it (either pointer may be NULL).  Synchronizes. */
+tt_fsi_status tt_fsi_batch_autotune(tt_fsi_batch batch, const void *v_dev, void *phi_dev,
+                                    struct CUstream_st *stream, int *tiles_per_item,
+                                    int *scores_per_item);
+/* Sets the work-item sizes directly. */
+tt_fsi_status tt_fsi_batch_set_schedule(tt_fsi_batch batch, int tiles_per_item, int scores_per_item);
+/* Bounded waits: polls before a score chunk gives up (default 4e6, about a
+ * second).  inject_missing_tile != 0 makes every wait expect one tile that is
+ * never produced -- for testing the timeout path only. */
+tt_fsi_status tt_fsi_batch_set_wait_limit(tt_fsi_batch batch, long long polls, int inject_missing_tile);
+/* Waits for the stream, reads and clears the batch's fault word (timeouts)
+ * and those of its plans. */
+tt_fsi_status tt_fsi_batch_check(tt_fsi_batch batch, struct CUstream_st *stream);
+
+/*
  * Masked-model games.  A GELU MLP f: R^d -> R^h1 -> R^h2 -> R,
  *   f(z) = W3 gelu(W2 gelu(W1 z + b1) + b2) + b3,  gelu(u) = u/2 (1 + erf(u/sqrt 2)),
  * with row-major float64 device weights W1 [h1, d], W2 [h2, h1], W3 [h2] and
@@ -199,6 +251,10 @@ tt_fsi_status tt_fsi_plan_check(tt_fsi_plan plan, struct CUstream_st *stream);
  */
 tt_fsi_status tt_fsi_apply_noalloc(int d, int ell, const double *v_dev, int64_t B,
                                    double *phi_dev, struct CUstream_st *stream);
+
+/* The CUDA runtime's description of the last CUDA error that made a call of
+ * this thread return TT_FSI_ERR_CUDA or TT_FSI_ERR_NO_MEMORY. */
+const char *tt_fsi_last_cuda_error(void);
 
 /* Human-readable name of a status. */
 const char *tt_fsi_status_string(tt_fsi_status status);

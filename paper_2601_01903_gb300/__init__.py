@@ -28,6 +28,8 @@ class FsiError(RuntimeError):
 
 def _check(status: int, what: str):
     if status != 0:
+        if status in (3, 4):
+            what = f"{what} [{native.load().tt_fsi_last_cuda_error().decode()}]"
         raise FsiError(status, what)
 
 
@@ -177,3 +179,73 @@ def masked_game(mlp, x, baseline, dtype=None, stream=None):
     out = torch.empty((B, 1 << dm.d), dtype=dtype or torch.float64, device=dm.W1.device)
     return masked_game_into(dm, torch.as_tensor(x, device=dm.W1.device),
                             torch.as_tensor(baseline, device=dm.W1.device), out, stream)
+
+
+class _Game(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("ell", ctypes.c_int), ("v_offset", ctypes.c_int64),
+                ("phi_offset", ctypes.c_int64)]
+
+
+class Batch:
+    """Many games of uneven size (d, l) in one persistent launch.  ``games``
+    is a sequence of (d, ell, v_offset, phi_offset), offsets in elements of
+    the batch's packed value and score buffers."""
+
+    def __init__(self, games, arith: str = "exact"):
+        self._lib = native.load()
+        self.arith = arith
+        arr = (_Game * len(games))(*[_Game(int(d), int(l), int(vo), int(po)) for d, l, vo, po in games])
+        h = ctypes.c_void_p()
+        _check(self._lib.tt_fsi_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(games), ARITH[arith],
+                                             ctypes.byref(h)), "tt_fsi_batch_create")
+        self._h = h
+        self.n_games = len(games)
+
+    @classmethod
+    def from_ragged(cls, g, arith: str = "exact"):
+        return cls([(int(g.d[k]), int(g.ell[k]), int(g.v_off[k]), int(g.phi_off[k]))
+                    for k in range(len(g.d))], arith)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.tt_fsi_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _call(self, name, v, phi, stream=None):
+        _check(getattr(self._lib, name)(self._h, ctypes.c_void_p(v.data_ptr()),
+                                        ctypes.c_void_p(phi.data_ptr()), _stream_ptr(stream)), name)
+        return phi
+
+    def apply(self, v, phi, stream=None):
+        """One persistent launch over every game (the batched path)."""
+        return self._call("tt_fsi_batch_apply", v, phi, stream)
+
+    def apply_per_game(self, v, phi, stream=None):
+        return self._call("tt_fsi_batch_apply_per_game", v, phi, stream)
+
+    def apply_graph(self, v, phi, stream=None):
+        return self._call("tt_fsi_batch_apply_graph", v, phi, stream)
+
+    def autotune(self, v, phi, stream=None):
+        t, c = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.tt_fsi_batch_autotune(self._h, ctypes.c_void_p(v.data_ptr()),
+                                               ctypes.c_void_p(phi.data_ptr()), _stream_ptr(stream),
+                                               ctypes.byref(t), ctypes.byref(c)), "tt_fsi_batch_autotune")
+        return t.value, c.value
+
+    def set_schedule(self, tiles_per_item: int, scores_per_item: int):
+        _check(self._lib.tt_fsi_batch_set_schedule(self._h, tiles_per_item, scores_per_item),
+               "tt_fsi_batch_set_schedule")
+
+    def set_wait_limit(self, polls: int, inject_missing_tile: bool = False):
+        _check(self._lib.tt_fsi_batch_set_wait_limit(self._h, polls, 1 if inject_missing_tile else 0),
+               "tt_fsi_batch_set_wait_limit")
+
+    def check(self, stream=None):
+        _check(self._lib.tt_fsi_batch_check(self._h, _stream_ptr(stream)), "tt_fsi_batch_check")

@@ -228,7 +228,7 @@ struct FastArgs {
     const float *wf32;
     int n_tab, n_g;
     int off_rec2, off_items2, off_rec3, off_items3, n_items2, n_items3;
-    int d, h, n_ch, ell, prec_bits, regA, regB;
+    int d, h, n_ch, ell, prec_bits, regA, regB, load_mask;
     long long game0;
 };
 
@@ -332,7 +332,7 @@ __device__ __forceinline__ void block3_item(const int32_t *rec, int u, const Acc
 }
 
 template <typename Acc>
-__global__ void __launch_bounds__(kTileThreads) fsi_tile_fast_kernel(FastArgs a) {
+__device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long long game, const long long tile) {
     using In = typename TileTraits<Acc>::In;
     using GT = typename GTraits<Acc>::G;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -343,8 +343,6 @@ __global__ void __launch_bounds__(kTileThreads) fsi_tile_fast_kernel(FastArgs a)
     __shared__ int s_emax;
 
     const int tid = threadIdx.x;
-    const long long game = a.game0 + blockIdx.y;
-    const long long tile = blockIdx.x;
     const In *src = reinterpret_cast<const In *>(a.v) + (game << a.d) + (tile << 12);
 
     for (int i = tid; i < a.n_tab; i += kTileThreads) stab[i] = __ldg(a.tab + i);
@@ -358,7 +356,7 @@ __global__ void __launch_bounds__(kTileThreads) fsi_tile_fast_kernel(FastArgs a)
         int emax = 0;
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
-            raw[r] = __ldg(src + tid + 256 * r);
+            raw[r] = __ldg(src + ((tid + 256 * r) & a.load_mask));
             emax = max(emax, (int)((raw[r] >> 52) & 0x7ff));
         }
         for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
@@ -374,7 +372,7 @@ __global__ void __launch_bounds__(kTileThreads) fsi_tile_fast_kernel(FastArgs a)
         for (int r = 0; r < 16; ++r) x[r] = bad ? 0ll : to_fixed(raw[r], E, a.prec_bits);
     } else {
 #pragma unroll
-        for (int r = 0; r < 16; ++r) x[r] = (Acc)__ldg(src + tid + 256 * r);
+        for (int r = 0; r < 16; ++r) x[r] = (Acc)__ldg(src + ((tid + 256 * r) & a.load_mask));
     }
     mobius16(x);
 #pragma unroll
@@ -483,6 +481,11 @@ __global__ void __launch_bounds__(kTileThreads) fsi_tile_fast_kernel(FastArgs a)
     }
 }
 
+template <typename Acc>
+__global__ void __launch_bounds__(kTileThreads) fsi_tile_fast_kernel(FastArgs a) {
+    tile_fast_body<Acc>(a, a.game0 + blockIdx.y, blockIdx.x);
+}
+
 // ----------------------------------------------------------------------------
 // Combine of the fast path: phi(S) = sum over tiles of G(S_L, s, |U_H n S_H|),
 // one warp per score, lanes over tiles.  Exact path: tile partial scores are
@@ -509,12 +512,14 @@ __device__ __forceinline__ __int128 shfl_down_i128(__int128 v, int o) {
     return (__int128)(((unsigned __int128)hi << 64) | lo);
 }
 
+// Scores [task_begin, task_end) of one game; warp w takes task_begin + w,
+// + kCombineFastWarps, ...  Partial scores are read past L1 (ld.global.cg):
+// in the persistent batch kernel other CTAs wrote them during this launch.
 template <typename Acc>
-__global__ void __launch_bounds__(32 * kCombineFastWarps) fsi_combine_fast_kernel(CombineFastArgs a) {
+__device__ __forceinline__ void combine_fast_body(const CombineFastArgs &a, const long long game,
+                                                  const long long task_begin, const long long task_end) {
     using GT = typename GTraits<Acc>::G;
-    const long long game = a.game0 + blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long task = (long long)blockIdx.x * kCombineFastWarps + warp;
     const int ntile = 1 << a.h;
     const GT *Gg = reinterpret_cast<const GT *>(a.G) + (game << a.h) * (long long)a.n_g;
     if constexpr (TileTraits<Acc>::exact) {
@@ -522,7 +527,7 @@ __global__ void __launch_bounds__(32 * kCombineFastWarps) fsi_combine_fast_kerne
         const int *texp = a.tile_exp + (game << a.h);
         int fmin = 0x7fffffff, fmax = -0x7fffffff;
         for (int u = threadIdx.x; u < ntile; u += blockDim.x) {
-            const int f = texp[u];
+            const int f = __ldcg(texp + u);
             fmin = min(fmin, f);
             fmax = max(fmax, f);
         }
@@ -534,35 +539,48 @@ __global__ void __launch_bounds__(32 * kCombineFastWarps) fsi_combine_fast_kerne
         atomicMin(&s_fmin, fmin);
         atomicMax(&s_fmax, fmax);
         __syncthreads();
-        if (task >= a.n_out) return;
         const int Fc = min(s_fmax, s_fmin + a.shift_cap);
-        const unsigned SH = (unsigned)a.tasks[task * 4 + 1];
-        const int s = a.tasks[task * 4 + 2] & 0xff;
-        const int gb = a.tasks[task * 4 + 3];
-        __int128 acc = 0;
-        for (int u = lane; u < ntile; u += 32) {
-            __int128 g = Gg[(long long)u * a.n_g + gb + __popc((unsigned)u & SH)];
-            const int delta = Fc - texp[u];
-            if (delta >= 0)
-                g = (__int128)((unsigned __int128)g << delta);
-            else
-                g = (-delta >= 127) ? (__int128)0 : ((g + ((__int128)1 << (-delta - 1))) >> (-delta));
-            acc += g;
-        }
-        for (int o = 16; o > 0; o >>= 1) acc += shfl_down_i128(acc, o);
-        if (lane == 0) {
-            const double r = i128_to_double(acc) / (double)a.wden[s];
-            reinterpret_cast<double *>(a.phi)[game * a.n_out + task] = ldexp(r, -Fc);
+        for (long long task = task_begin + warp; task < task_end; task += kCombineFastWarps) {
+            const unsigned SH = (unsigned)a.tasks[task * 4 + 1];
+            const int s = a.tasks[task * 4 + 2] & 0xff;
+            const int gb = a.tasks[task * 4 + 3];
+            __int128 acc = 0;
+            for (int u = lane; u < ntile; u += 32) {
+                const GT *gp = Gg + (long long)u * a.n_g + gb + __popc((unsigned)u & SH);
+                const longlong2 raw = __ldcg(reinterpret_cast<const longlong2 *>(gp));
+                __int128 g = (__int128)(((unsigned __int128)(unsigned long long)raw.y << 64) |
+                                        (unsigned long long)raw.x);
+                const int delta = Fc - __ldcg(texp + u);
+                if (delta >= 0)
+                    g = (__int128)((unsigned __int128)g << delta);
+                else
+                    g = (-delta >= 127) ? (__int128)0 : ((g + ((__int128)1 << (-delta - 1))) >> (-delta));
+                acc += g;
+            }
+            for (int o = 16; o > 0; o >>= 1) acc += shfl_down_i128(acc, o);
+            if (lane == 0) {
+                const double r = i128_to_double(acc) / (double)a.wden[s];
+                reinterpret_cast<double *>(a.phi)[game * a.n_out + task] = ldexp(r, -Fc);
+            }
         }
     } else {
-        if (task >= a.n_out) return;
-        const unsigned SH = (unsigned)a.tasks[task * 4 + 1];
-        const int gb = a.tasks[task * 4 + 3];
-        Acc acc = 0;
-        for (int u = lane; u < ntile; u += 32) acc += Gg[(long long)u * a.n_g + gb + __popc((unsigned)u & SH)];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        if (lane == 0) reinterpret_cast<Acc *>(a.phi)[game * a.n_out + task] = acc;
+        for (long long task = task_begin + warp; task < task_end; task += kCombineFastWarps) {
+            const unsigned SH = (unsigned)a.tasks[task * 4 + 1];
+            const int gb = a.tasks[task * 4 + 3];
+            Acc acc = 0;
+            for (int u = lane; u < ntile; u += 32)
+                acc += __ldcg(Gg + (long long)u * a.n_g + gb + __popc((unsigned)u & SH));
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+            if (lane == 0) reinterpret_cast<Acc *>(a.phi)[game * a.n_out + task] = acc;
+        }
     }
+}
+
+template <typename Acc>
+__global__ void __launch_bounds__(32 * kCombineFastWarps) fsi_combine_fast_kernel(CombineFastArgs a) {
+    const long long t0 = (long long)blockIdx.x * kCombineFastWarps;
+    const long long t1 = (t0 + kCombineFastWarps < a.n_out) ? t0 + kCombineFastWarps : a.n_out;
+    combine_fast_body<Acc>(a, a.game0 + blockIdx.y, t0, t1);
 }
 
 // ----------------------------------------------------------------------------
@@ -671,10 +689,25 @@ __global__ void __launch_bounds__(kCombineThreads) fsi_combine_kernel(CombineArg
 // ----------------------------------------------------------------------------
 namespace {
 
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
 tt_fsi_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return TT_FSI_OK;
+    g_last_cuda_error = e;
     if (e == cudaErrorMemoryAllocation) return TT_FSI_ERR_NO_MEMORY;
     return TT_FSI_ERR_CUDA;
+}
+
+// Raises a kernel's dynamic shared-memory cap to the device's opt-in maximum.
+// The cap is per kernel, not per plan, so it must never be lowered by a plan
+// that needs less than another plan created earlier.
+template <typename K>
+cudaError_t allow_max_smem(K *kernel) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024);
+    return e;
 }
 
 // Every device-side table of a plan, so that plan creation and the
@@ -803,6 +836,7 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
             fa.prec_bits = p.prec_bits;
             fa.regA = std::max(1 << p.b, p.n8 * 16);
             fa.regB = std::max(p.n4 * 256, p.n_ch);
+            fa.load_mask = (1 << p.load_bits) - 1;
             fa.game0 = g0;
             fsi_tile_fast_kernel<Acc><<<g1, kTileThreads, p.smem_fast, st>>>(fa);
         } else {
@@ -921,11 +955,11 @@ tt_fsi_status tt_fsi_plan_create(int d, int ell, tt_fsi_arith arith, int64_t max
         }
         const int smem = (int)p.smem_tile;
         if (arith == TT_FSI_ARITH_EXACT)
-            e = cudaFuncSetAttribute(fsi_tile_kernel<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            e = allow_max_smem(fsi_tile_kernel<long long>);
         else if (arith == TT_FSI_ARITH_F64)
-            e = cudaFuncSetAttribute(fsi_tile_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            e = allow_max_smem(fsi_tile_kernel<double>);
         else
-            e = cudaFuncSetAttribute(fsi_tile_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            e = allow_max_smem(fsi_tile_kernel<float>);
         if (e != cudaSuccess) {
             st = cuda_status(e);
             break;
@@ -933,11 +967,11 @@ tt_fsi_status tt_fsi_plan_create(int d, int ell, tt_fsi_arith arith, int64_t max
         if (p.fast12) {
             const int fsm = (int)p.smem_fast;
             if (arith == TT_FSI_ARITH_EXACT)
-                e = cudaFuncSetAttribute(fsi_tile_fast_kernel<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+                e = allow_max_smem(fsi_tile_fast_kernel<long long>);
             else if (arith == TT_FSI_ARITH_F64)
-                e = cudaFuncSetAttribute(fsi_tile_fast_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+                e = allow_max_smem(fsi_tile_fast_kernel<double>);
             else
-                e = cudaFuncSetAttribute(fsi_tile_fast_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+                e = allow_max_smem(fsi_tile_fast_kernel<float>);
             if (e != cudaSuccess) {
                 st = cuda_status(e);
                 break;
@@ -1062,6 +1096,8 @@ tt_fsi_status tt_fsi_plan_check(tt_fsi_plan plan, struct CUstream_st *stream) {
     return TT_FSI_OK;
 }
 
+const char *tt_fsi_last_cuda_error(void) { return cudaGetErrorString(ttfsi::g_last_cuda_error); }
+
 const char *tt_fsi_status_string(tt_fsi_status s) {
     switch (s) {
         case TT_FSI_OK: return "ok";
@@ -1155,10 +1191,8 @@ extern "C" tt_fsi_status tt_fsi_apply_noalloc(int d, int ell, const double *v_de
     if (!g_na_base[dev]) {
         void *ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return TT_FSI_ERR_CUDA;
-        if (cudaFuncSetAttribute(fsi_tile_kernel<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 224 * 1024) != cudaSuccess ||
-            cudaFuncSetAttribute(fsi_tile_fast_kernel<long long>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024) != cudaSuccess)
+        if (allow_max_smem(fsi_tile_kernel<long long>) != cudaSuccess ||
+            allow_max_smem(fsi_tile_fast_kernel<long long>) != cudaSuccess)
             return TT_FSI_ERR_CUDA;
         g_na_base[dev] = static_cast<unsigned char *>(ptr);
     }
@@ -1181,3 +1215,516 @@ extern "C" tt_fsi_status tt_fsi_apply_noalloc(int d, int ell, const double *v_de
     noalloc_poison_kernel<<<64, 256, 0, st>>>(p.d_err, phi_dev, (long long)B * p.n_out);
     return cuda_status(cudaGetLastError());
 }
+
+// ============================================================================
+// Batches of uneven games (different d and l) in one persistent launch.
+//
+// Work items: first the tiles of every game (largest games first, a few
+// consecutive tiles per item), then the score chunks of every game.  One CTA
+// per SM pulls items from a device counter.  A score chunk of game g needs
+// every tile of g: its CTA waits on g's finished-tile counter with a bounded
+// number of polls; every tile it waits for was handed out earlier to a CTA
+// that is running and never waits itself, so the wait ends unless something
+// is broken -- then the kernel records TT_FSI_ERR_TIMEOUT and the remaining
+// waits give up at once.
+// ============================================================================
+#include <memory>
+
+namespace ttfsi {
+namespace {
+
+enum : int { kErrTimeout = 2 };
+
+struct BatchGameDev {
+    long long v_off, phi_off, g_off, exp_off;  // element offsets into v, phi, partial scores, exponents
+    int plan, n_tiles;
+};
+
+struct BatchItem {
+    int game, first, count;  // tiles [first, first + count) or scores [first, first + count)
+};
+
+struct BatchArgs {
+    const void *v;
+    void *phi;
+    void *G;
+    int *tile_exp;
+    int *err;
+    const FastArgs *fplans;
+    const CombineFastArgs *cplans;
+    const BatchGameDev *games;
+    const BatchItem *items;
+    int n_tile_items, n_items;
+    int *head;
+    int *done;
+    long long spin_limit;
+    int inject_missing;  // test hook: every wait expects one tile more than exists
+};
+
+template <typename Acc>
+__global__ void __launch_bounds__(kTileThreads) fsi_batch_kernel(BatchArgs a) {
+    using GT = typename GTraits<Acc>::G;
+    using In = typename TileTraits<Acc>::In;
+    using Out = typename std::conditional<sizeof(Acc) == 4, float, double>::type;
+    __shared__ int s_item, s_ok;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(a.head, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= a.n_items) break;
+        const BatchItem it = a.items[item];
+        const BatchGameDev g = a.games[it.game];
+        if (item < a.n_tile_items) {
+            FastArgs fa = a.fplans[g.plan];
+            fa.v = reinterpret_cast<const In *>(a.v) + g.v_off;
+            fa.G = reinterpret_cast<GT *>(a.G) + g.g_off;
+            fa.tile_exp = a.tile_exp + g.exp_off;
+            fa.err = a.err;
+            for (int t = it.first; t < it.first + it.count; ++t) {
+                tile_fast_body<Acc>(fa, 0, t);
+                __syncthreads();
+            }
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) atomicAdd(a.done + it.game, it.count);
+        } else {
+            if (threadIdx.x == 0) {
+                const int need = g.n_tiles + (a.inject_missing ? 1 : 0);
+                int ok = 1;
+                long long polls = 0;
+                while (atomicAdd(a.done + it.game, 0) < need) {
+                    if ((atomicAdd(a.err, 0) & kErrTimeout) || ++polls > a.spin_limit) {
+                        atomicOr(a.err, kErrTimeout);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(200);
+                }
+                __threadfence();
+                s_ok = ok;
+            }
+            __syncthreads();
+            if (s_ok) {
+                CombineFastArgs ca = a.cplans[g.plan];
+                ca.G = reinterpret_cast<GT *>(a.G) + g.g_off;
+                ca.tile_exp = a.tile_exp + g.exp_off;
+                ca.phi = reinterpret_cast<Out *>(a.phi) + g.phi_off;
+                combine_fast_body<Acc>(ca, 0, it.first, it.first + it.count);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace
+}  // namespace ttfsi
+
+struct tt_fsi_batch_s {
+    tt_fsi_arith arith = TT_FSI_ARITH_EXACT;
+    std::vector<tt_fsi_game> games;
+    std::vector<tt_fsi_plan> plans;                // one per distinct (d, l)
+    std::vector<int> plan_of_game;
+    std::vector<ttfsi::BatchGameDev> hgames;
+    std::vector<int> fast_games, slow_games;
+    int tiles_per_item = 1, scores_per_item = 64;
+    int n_tile_items = 0, n_items = 0;
+    ttfsi::FastArgs *d_fplans = nullptr;
+    ttfsi::CombineFastArgs *d_cplans = nullptr;
+    ttfsi::BatchGameDev *d_games = nullptr;
+    ttfsi::BatchItem *d_items = nullptr;
+    int *d_counters = nullptr;  // [0] queue head, [1 + g] finished tiles of game g
+    int *d_err = nullptr;
+    void *d_G = nullptr;
+    int *d_exp = nullptr;
+    size_t smem = 0;
+    int grid = 0;
+    long long spin_limit = 4000000;
+    int inject_missing = 0;
+    cudaGraphExec_t graph = nullptr;
+    cudaGraph_t graph_def = nullptr;
+    const void *graph_v = nullptr;
+    void *graph_phi = nullptr;
+};
+
+namespace ttfsi {
+namespace {
+
+size_t in_elem(tt_fsi_arith a) { return a == TT_FSI_ARITH_F32 ? 4 : 8; }
+size_t g_elem(tt_fsi_arith a) { return a == TT_FSI_ARITH_EXACT ? 16 : (a == TT_FSI_ARITH_F64 ? 8 : 4); }
+
+// Builds the work list for the current item sizes and uploads it.
+tt_fsi_status batch_build_items(tt_fsi_batch_s *b) {
+    std::vector<int> order = b->fast_games;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return b->hgames[x].n_tiles > b->hgames[y].n_tiles;
+    });
+    std::vector<BatchItem> items;
+    for (int g : order)
+        for (int t = 0; t < b->hgames[g].n_tiles; t += b->tiles_per_item)
+            items.push_back({g, t, std::min(b->tiles_per_item, b->hgames[g].n_tiles - t)});
+    b->n_tile_items = (int)items.size();
+    for (int g : order) {
+        const int64_t n_out = b->plans[b->plan_of_game[g]]->p.n_out;
+        for (int64_t t = 0; t < n_out; t += b->scores_per_item)
+            items.push_back({g, (int)t, (int)std::min<int64_t>(b->scores_per_item, n_out - t)});
+    }
+    b->n_items = (int)items.size();
+    cudaFree(b->d_items);
+    b->d_items = nullptr;
+    if (items.empty()) return TT_FSI_OK;
+    cudaError_t e = cudaMalloc((void **)&b->d_items, items.size() * sizeof(BatchItem));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
+    return cuda_status(e);
+}
+
+void batch_free(tt_fsi_batch_s *b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->graph_def) cudaGraphDestroy(b->graph_def);
+    cudaFree(b->d_fplans);
+    cudaFree(b->d_cplans);
+    cudaFree(b->d_games);
+    cudaFree(b->d_items);
+    cudaFree(b->d_counters);
+    cudaFree(b->d_err);
+    cudaFree(b->d_G);
+    cudaFree(b->d_exp);
+    for (tt_fsi_plan p : b->plans) tt_fsi_plan_destroy(p);
+}
+
+template <typename Acc>
+tt_fsi_status batch_launch(tt_fsi_batch_s *b, const void *v, void *phi, cudaStream_t st) {
+    if (b->n_items > 0) {
+        const size_t nc = 1 + b->games.size();
+        cudaError_t e = cudaMemsetAsync(b->d_counters, 0, nc * sizeof(int), st);
+        if (e != cudaSuccess) return cuda_status(e);
+        BatchArgs a{};
+        a.v = v;
+        a.phi = phi;
+        a.G = b->d_G;
+        a.tile_exp = b->d_exp;
+        a.err = b->d_err;
+        a.fplans = b->d_fplans;
+        a.cplans = b->d_cplans;
+        a.games = b->d_games;
+        a.items = b->d_items;
+        a.n_tile_items = b->n_tile_items;
+        a.n_items = b->n_items;
+        a.head = b->d_counters;
+        a.done = b->d_counters + 1;
+        a.spin_limit = b->spin_limit;
+        a.inject_missing = b->inject_missing;
+        fsi_batch_kernel<Acc><<<b->grid, kTileThreads, b->smem, st>>>(a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    // games outside the fast path (l > 3 or l >= d): one plan call each
+    const size_t ie = in_elem(b->arith);
+    for (int g : b->slow_games) {
+        const tt_fsi_game &gm = b->games[g];
+        tt_fsi_status s = tt_fsi_apply(b->plans[b->plan_of_game[g]], (const char *)v + gm.v_offset * ie, 1,
+                                       (char *)phi + gm.phi_offset * ie, reinterpret_cast<CUstream_st *>(st));
+        if (s != TT_FSI_OK) return s;
+    }
+    return TT_FSI_OK;
+}
+
+}  // namespace
+}  // namespace ttfsi
+
+extern "C" {
+
+tt_fsi_status tt_fsi_batch_create(const tt_fsi_game *games_host, int64_t n_games, tt_fsi_arith arith,
+                                  tt_fsi_batch *out) {
+    using namespace ttfsi;
+    if (!out || n_games < 0 || (n_games > 0 && !games_host)) return TT_FSI_ERR_INVALID_ARG;
+    if (arith != TT_FSI_ARITH_EXACT && arith != TT_FSI_ARITH_F64 && arith != TT_FSI_ARITH_F32)
+        return TT_FSI_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::unique_ptr<tt_fsi_batch_s> b(new (std::nothrow) tt_fsi_batch_s());
+    if (!b) return TT_FSI_ERR_NO_MEMORY;
+    b->arith = arith;
+    b->games.assign(games_host, games_host + n_games);
+    std::map<std::pair<int, int>, int> plan_idx;
+    tt_fsi_status st = TT_FSI_OK;
+    for (int64_t g = 0; g < n_games && st == TT_FSI_OK; ++g) {
+        const tt_fsi_game &gm = b->games[g];
+        if (gm.d < 1 || gm.d > 30 || gm.ell < 1 || gm.v_offset < 0 || gm.phi_offset < 0) {
+            st = TT_FSI_ERR_INVALID_ARG;
+            break;
+        }
+        auto key = std::make_pair(gm.d, gm.ell);
+        auto it = plan_idx.find(key);
+        if (it == plan_idx.end()) {
+            tt_fsi_plan p = nullptr;
+            st = tt_fsi_plan_create(gm.d, gm.ell, arith, 1, &p);
+            if (st != TT_FSI_OK) break;
+            it = plan_idx.emplace(key, (int)b->plans.size()).first;
+            b->plans.push_back(p);
+        }
+        b->plan_of_game.push_back(it->second);
+    }
+    if (st != TT_FSI_OK) {
+        batch_free(b.get());
+        return st;
+    }
+    // per-game offsets of the partial scores and exponents
+    long long goff = 0, eoff = 0;
+    b->hgames.resize(n_games);
+    for (int64_t g = 0; g < n_games; ++g) {
+        const Plan &p = b->plans[b->plan_of_game[g]]->p;
+        BatchGameDev &hg = b->hgames[g];
+        hg.v_off = b->games[g].v_offset;
+        hg.phi_off = b->games[g].phi_offset;
+        hg.plan = b->plan_of_game[g];
+        hg.n_tiles = 1 << p.h;
+        hg.g_off = goff;
+        hg.exp_off = eoff;
+        if (p.fast12) {
+            b->fast_games.push_back((int)g);
+            goff += (long long)hg.n_tiles * p.n_g;
+            eoff += hg.n_tiles;
+            b->smem = std::max(b->smem, p.smem_fast);
+        } else {
+            b->slow_games.push_back((int)g);
+        }
+    }
+    // device copies of each plan's kernel arguments
+    std::vector<FastArgs> fpl(b->plans.size());
+    std::vector<CombineFastArgs> cpl(b->plans.size());
+    for (size_t i = 0; i < b->plans.size(); ++i) {
+        const Plan &p = b->plans[i]->p;
+        FastArgs &fa = fpl[i];
+        fa = FastArgs{};
+        fa.tab = p.d_fast_tab;
+        fa.gtab = p.d_gtab;
+        fa.wnum = p.d_wnum;
+        fa.wden = p.d_wden;
+        fa.wf64 = p.d_wf64;
+        fa.wf32 = p.d_wf32;
+        fa.n_tab = (int)p.fast_tab.size();
+        fa.n_g = p.n_g;
+        fa.off_rec2 = p.off_rec2;
+        fa.off_items2 = p.off_items2;
+        fa.off_rec3 = p.off_rec3;
+        fa.off_items3 = p.off_items3;
+        fa.n_items2 = p.n_items2;
+        fa.n_items3 = p.n_items3;
+        fa.d = p.d;
+        fa.h = p.h;
+        fa.n_ch = p.n_ch;
+        fa.ell = p.ell;
+        fa.prec_bits = p.prec_bits;
+        fa.regA = std::max(1 << p.b, p.n8 * 16);
+        fa.regB = std::max(p.n4 * 256, p.n_ch);
+        fa.load_mask = (1 << p.load_bits) - 1;
+        CombineFastArgs &ca = cpl[i];
+        ca = CombineFastArgs{};
+        ca.tasks = p.d_tasks;
+        ca.wden = p.d_wden;
+        ca.h = p.h;
+        ca.n_g = p.n_g;
+        ca.shift_cap = p.shift_cap;
+        ca.n_out = p.n_out;
+    }
+    cudaError_t e = cudaSuccess;
+    auto up = [&](void **dst, const void *src, size_t bytes) {
+        if (e != cudaSuccess || bytes == 0) return;
+        e = cudaMalloc(dst, bytes);
+        if (e == cudaSuccess) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    up((void **)&b->d_fplans, fpl.data(), fpl.size() * sizeof(FastArgs));
+    up((void **)&b->d_cplans, cpl.data(), cpl.size() * sizeof(CombineFastArgs));
+    up((void **)&b->d_games, b->hgames.data(), b->hgames.size() * sizeof(BatchGameDev));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_counters, (1 + (size_t)n_games) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
+    if (e == cudaSuccess && goff > 0) e = cudaMalloc(&b->d_G, (size_t)goff * g_elem(arith));
+    if (e == cudaSuccess && eoff > 0) e = cudaMalloc((void **)&b->d_exp, (size_t)eoff * sizeof(int));
+    if (e == cudaSuccess && !b->fast_games.empty()) {
+        int occ = 0, dev = 0, sms = 0;
+        if (arith == TT_FSI_ARITH_EXACT) {
+            e = allow_max_smem(fsi_batch_kernel<long long>);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fsi_batch_kernel<long long>, kTileThreads, b->smem);
+        } else if (arith == TT_FSI_ARITH_F64) {
+            e = allow_max_smem(fsi_batch_kernel<double>);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fsi_batch_kernel<double>, kTileThreads, b->smem);
+        } else {
+            e = allow_max_smem(fsi_batch_kernel<float>);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fsi_batch_kernel<float>, kTileThreads, b->smem);
+        }
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        b->grid = std::max(1, occ) * sms;  // every CTA resident at once: waits can always be served
+        if (occ < 1) e = cudaErrorInvalidConfiguration;
+    }
+    st = cuda_status(e);
+    if (st == TT_FSI_OK) st = batch_build_items(b.get());
+    if (st != TT_FSI_OK) {
+        batch_free(b.get());
+        return st;
+    }
+    *out = b.release();
+    return TT_FSI_OK;
+}
+
+void tt_fsi_batch_destroy(tt_fsi_batch batch) {
+    if (!batch) return;
+    cudaDeviceSynchronize();
+    ttfsi::batch_free(batch);
+    delete batch;
+}
+
+tt_fsi_status tt_fsi_batch_apply(tt_fsi_batch b, const void *v_dev, void *phi_dev, struct CUstream_st *stream) {
+    using namespace ttfsi;
+    if (!b) return TT_FSI_ERR_INVALID_ARG;
+    if (b->games.empty()) return TT_FSI_OK;
+    if (!v_dev || !phi_dev) return TT_FSI_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    switch (b->arith) {
+        case TT_FSI_ARITH_EXACT: return batch_launch<long long>(b, v_dev, phi_dev, st);
+        case TT_FSI_ARITH_F64: return batch_launch<double>(b, v_dev, phi_dev, st);
+        case TT_FSI_ARITH_F32: return batch_launch<float>(b, v_dev, phi_dev, st);
+    }
+    return TT_FSI_ERR_INVALID_ARG;
+}
+
+tt_fsi_status tt_fsi_batch_apply_per_game(tt_fsi_batch b, const void *v_dev, void *phi_dev,
+                                          struct CUstream_st *stream) {
+    using namespace ttfsi;
+    if (!b) return TT_FSI_ERR_INVALID_ARG;
+    if (b->games.empty()) return TT_FSI_OK;
+    if (!v_dev || !phi_dev) return TT_FSI_ERR_INVALID_ARG;
+    const size_t ie = in_elem(b->arith);
+    for (size_t g = 0; g < b->games.size(); ++g) {
+        const tt_fsi_game &gm = b->games[g];
+        tt_fsi_status s = tt_fsi_apply(b->plans[b->plan_of_game[g]], (const char *)v_dev + gm.v_offset * ie, 1,
+                                       (char *)phi_dev + gm.phi_offset * ie, stream);
+        if (s != TT_FSI_OK) return s;
+    }
+    return TT_FSI_OK;
+}
+
+tt_fsi_status tt_fsi_batch_apply_graph(tt_fsi_batch b, const void *v_dev, void *phi_dev,
+                                       struct CUstream_st *stream) {
+    using namespace ttfsi;
+    if (!b) return TT_FSI_ERR_INVALID_ARG;
+    if (b->games.empty()) return TT_FSI_OK;
+    if (!v_dev || !phi_dev) return TT_FSI_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!b->graph || b->graph_v != v_dev || b->graph_phi != phi_dev) {
+        if (b->graph) cudaGraphExecDestroy(b->graph);
+        if (b->graph_def) cudaGraphDestroy(b->graph_def);
+        b->graph = nullptr;
+        b->graph_def = nullptr;
+        cudaStream_t cap = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_status(e);
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        tt_fsi_status s = TT_FSI_OK;
+        if (e == cudaSuccess) s = tt_fsi_batch_apply_per_game(b, v_dev, phi_dev, reinterpret_cast<CUstream_st *>(cap));
+        cudaGraph_t gdef = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cap, &gdef);
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess || e2 != cudaSuccess || s != TT_FSI_OK) {
+            if (gdef) cudaGraphDestroy(gdef);
+            return s != TT_FSI_OK ? s : cuda_status(e != cudaSuccess ? e : e2);
+        }
+        e = cudaGraphInstantiate(&b->graph, gdef, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(gdef);
+            b->graph = nullptr;
+            return cuda_status(e);
+        }
+        b->graph_def = gdef;
+        b->graph_v = v_dev;
+        b->graph_phi = phi_dev;
+    }
+    return cuda_status(cudaGraphLaunch(b->graph, st));
+}
+
+tt_fsi_status tt_fsi_batch_autotune(tt_fsi_batch b, const void *v_dev, void *phi_dev, struct CUstream_st *stream,
+                                    int *tiles_per_item, int *scores_per_item) {
+    using namespace ttfsi;
+    if (!b || !v_dev || !phi_dev) return TT_FSI_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int tpi[] = {1, 2, 4, 8};
+    const int spi[] = {16, 64, 256};
+    float best = 1e30f;
+    int bt = b->tiles_per_item, bs = b->scores_per_item;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return TT_FSI_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return TT_FSI_ERR_CUDA;
+    }
+    tt_fsi_status s = TT_FSI_OK;
+    for (int t : tpi) {
+        for (int c : spi) {
+            b->tiles_per_item = t;
+            b->scores_per_item = c;
+            if ((s = batch_build_items(b)) != TT_FSI_OK) break;
+            if ((s = tt_fsi_batch_apply(b, v_dev, phi_dev, stream)) != TT_FSI_OK) break;  // warm-up
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 3 && s == TT_FSI_OK; ++r) s = tt_fsi_batch_apply(b, v_dev, phi_dev, stream);
+            cudaEventRecord(e1, st);
+            if (s != TT_FSI_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+                if (s == TT_FSI_OK) s = TT_FSI_ERR_CUDA;
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bt = t;
+                bs = c;
+            }
+        }
+        if (s != TT_FSI_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->tiles_per_item = bt;
+    b->scores_per_item = bs;
+    tt_fsi_status s2 = batch_build_items(b);
+    if (s == TT_FSI_OK) s = s2;
+    if (tiles_per_item) *tiles_per_item = bt;
+    if (scores_per_item) *scores_per_item = bs;
+    return s;
+}
+
+tt_fsi_status tt_fsi_batch_set_schedule(tt_fsi_batch b, int tiles_per_item, int scores_per_item) {
+    if (!b || tiles_per_item < 1 || scores_per_item < 1) return TT_FSI_ERR_INVALID_ARG;
+    b->tiles_per_item = tiles_per_item;
+    b->scores_per_item = scores_per_item;
+    return ttfsi::batch_build_items(b);
+}
+
+tt_fsi_status tt_fsi_batch_set_wait_limit(tt_fsi_batch b, long long polls, int inject_missing_tile) {
+    if (!b || polls < 1) return TT_FSI_ERR_INVALID_ARG;
+    b->spin_limit = polls;
+    b->inject_missing = inject_missing_tile ? 1 : 0;
+    return TT_FSI_OK;
+}
+
+tt_fsi_status tt_fsi_batch_check(tt_fsi_batch b, struct CUstream_st *stream) {
+    using namespace ttfsi;
+    if (!b) return TT_FSI_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int h_err = 0;
+    cudaError_t e = cudaMemcpyAsync(&h_err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (tt_fsi_plan p : b->plans) {
+        tt_fsi_status s = tt_fsi_plan_check(p, stream);
+        if (s != TT_FSI_OK) h_err |= (s == TT_FSI_ERR_NONFINITE) ? kErrNonFinite : 0;
+    }
+    if (h_err & kErrTimeout) return TT_FSI_ERR_TIMEOUT;
+    if (h_err & kErrNonFinite) return TT_FSI_ERR_NONFINITE;
+    return TT_FSI_OK;
+}
+
+}  // extern "C"

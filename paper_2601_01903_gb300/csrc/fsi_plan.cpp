@@ -141,10 +141,20 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
     const size_t elem = (arith == TT_FSI_ARITH_F32) ? 4 : 8;
     const size_t smem_budget = 224 * 1024;  // 227 KB opt-in per CTA, minus static
 
-    // Tile width: the largest b <= min(d, 12) whose two ranked-sum buffers
-    // fit in shared memory.
-    int b = std::min(d, kMaxTileBits);
+    // Tile width.  Orders l <= 3 (below d) take the fast path, whose tile is
+    // always 12 bits: a game with d < 12 is processed as the 12-player game
+    // with 12 - d null players appended (v_ext(S) = v(S n [d])); its
+    // Moebius coefficients vanish on every T that contains a null player and
+    // Eq. correction's weights depend only on |S| and |T|, so the scores of
+    // the sets inside [d] are unchanged.  Otherwise: the largest b <=
+    // min(d, 12) whose two ranked-sum buffers fit in shared memory.
+    const bool want_fast = !p.mob_only && ell <= 3;
+    int b = want_fast ? kMaxTileBits : std::min(d, kMaxTileBits);
     for (;; --b) {
+        if (want_fast) {
+            p.buf_elems = 1 << b;
+            break;
+        }
         // state count after k processed bits: sum_{s <= min(k, l)} C(k, s)(k - s + 1)
         const Pascal &C = pascal();
         int64_t peak = (int64_t)1 << b;
@@ -161,7 +171,8 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
         }
     }
     p.b = b;
-    p.h = d - b;
+    p.h = std::max(0, d - b);
+    p.load_bits = std::min(d, b);
     p.smem_tile = (size_t)p.buf_elems * 2 * elem;
 
     // ---------------- ranked superset states and transitions --------------
@@ -213,7 +224,7 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
     }
 
     // fast tile path tables (see fsi_plan.h)
-    if (!p.mob_only && b == kMaxTileBits && ell <= 3) {
+    if (want_fast) {
         auto states_at = [&](int k) {
             std::vector<std::pair<uint32_t, int>> st;
             for (uint32_t sg = 0; sg < (1u << k); ++sg) {
@@ -320,6 +331,7 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
         }
         p.smem_fast += (p.fast_tab.size() + p.gtab.size()) * sizeof(int32_t);
         p.fast12 = p.smem_fast <= smem_budget;
+        if (!p.fast12) return TT_FSI_ERR_UNSUPPORTED;  // does not happen for l <= 3
     }
 
     // ---------------- combined weights omega_s(p, q) ----------------------

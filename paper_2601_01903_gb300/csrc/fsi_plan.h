@@ -35,7 +35,8 @@ struct Plan {
     int d = 0, ell = 0, ell_eff = 0;
     tt_fsi_arith arith = TT_FSI_ARITH_EXACT;
     int64_t max_batch = 0;
-    int b = 0, h = 0;         // tile bits, high bits (d = b + h)
+    int b = 0, h = 0;         // tile bits, high bits (d = b + h, or d < b = 12 on the fast path)
+    int load_bits = 0;        // bits of a tile present in v (min(d, b)); the rest are null players
     bool mob_only = false;    // l >= d: scores are the Moebius coefficients
     int64_t n_out = 0;        // scores per game
     int n_ch = 0;             // channels per tile (states at the last level)

@@ -120,6 +120,8 @@ def _declare(lib):
     lib.tt_fsi_apply.argtypes = [vp, vp, i64, vp, vp]
     lib.tt_fsi_plan_check.restype = i
     lib.tt_fsi_plan_check.argtypes = [vp, vp]
+    lib.tt_fsi_last_cuda_error.restype = c.c_char_p
+    lib.tt_fsi_last_cuda_error.argtypes = []
     lib.tt_fsi_status_string.restype = c.c_char_p
     lib.tt_fsi_status_string.argtypes = [i]
     lib.tt_fsi_apply_host.restype = i
@@ -133,6 +135,21 @@ def _declare(lib):
     lib.tt_fsi_masked_game.argtypes = [vp, vp, vp, i64, vp, i, vp]
     lib.tt_fsi_apply_noalloc.restype = i
     lib.tt_fsi_apply_noalloc.argtypes = [i, i, vp, i64, vp, vp]
+    for name in ("tt_fsi_batch_apply", "tt_fsi_batch_apply_per_game", "tt_fsi_batch_apply_graph"):
+        getattr(lib, name).restype = i
+        getattr(lib, name).argtypes = [vp, vp, vp, vp]
+    lib.tt_fsi_batch_create.restype = i
+    lib.tt_fsi_batch_create.argtypes = [vp, i64, i, c.POINTER(vp)]
+    lib.tt_fsi_batch_destroy.restype = None
+    lib.tt_fsi_batch_destroy.argtypes = [vp]
+    lib.tt_fsi_batch_autotune.restype = i
+    lib.tt_fsi_batch_autotune.argtypes = [vp, vp, vp, vp, c.POINTER(i), c.POINTER(i)]
+    lib.tt_fsi_batch_set_schedule.restype = i
+    lib.tt_fsi_batch_set_schedule.argtypes = [vp, i, i]
+    lib.tt_fsi_batch_set_wait_limit.restype = i
+    lib.tt_fsi_batch_set_wait_limit.argtypes = [vp, c.c_longlong, i]
+    lib.tt_fsi_batch_check.restype = i
+    lib.tt_fsi_batch_check.argtypes = [vp, vp]
     for name, args, res in EXTRA_SIGNATURES:
         fn = getattr(lib, name, None)
         if fn is not None:
