@@ -42,6 +42,11 @@ def parse():
     ap.add_argument("--arith", default="exact", choices=["exact", "f64", "f32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--workload", default="mlp_d20_l3_b16",
+                    choices=["mlp_d20_l3_b16", "uneven_1024"],
+                    help="mlp_d20_l3_b16: the headline batch; uneven_1024: 1024 Moebius-sparse "
+                         "games with d in 10..20 and l in 1..3, one persistent launch vs "
+                         "per-game launches vs a CUDA graph of them")
     return ap.parse_args()
 
 
@@ -306,6 +311,63 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_uneven(args, rank, world, local_rank):
+    """1024 uneven games: the persistent batched launch (autotuned schedule)
+    timed against one tt_fsi_apply per game and against a CUDA graph of
+    those launches."""
+    import torch
+    import paper_2601_01903_gb300 as fsi
+    from paper_2601_01903_gb300 import synthetic
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    g = synthetic.workload_uneven()
+    v = torch.as_tensor(g.v, device=dev)
+    phi = torch.zeros(g.n_phi, dtype=torch.float64, device=dev)
+    b = fsi.Batch.from_ragged(g, arith=args.arith if args.arith != "f32" else "exact")
+    tpi, spi = b.autotune(v, phi)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn(v, phi)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn(v, phi)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / steps
+
+    with ClockSampler(local_rank) as clocks:
+        ms_p = timed(b.apply, args.steps)
+    b.check()
+    ref_steps = max(3, min(args.steps, 10))
+    ms_g = timed(b.apply_per_game, ref_steps)
+    ms_c = timed(b.apply_graph, ref_steps)
+    b.check()
+    coal = float(sum(1 << int(x) for x in g.d))
+    peak, peak_kind = peaks()
+    achieved = g.v.nbytes / (ms_p * 1e-3) / 1e9
+    if rank != 0:
+        return
+    line = {
+        "metric": "batched uneven FSI coalitions/s (one persistent launch)", "value": coal / (ms_p * 1e-3),
+        "unit": "coalitions/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_p, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"exact": "int64", "f64": "f64", "f32": "int64"}[args.arith], "data": "synthetic",
+        "config": {"workload": "uneven_1024", "games": len(g.d), "d": "U{10..20}", "ell": "U{1,2,3}",
+                   "coalitions": coal, "scores": g.n_phi, "tiles_per_item": tpi, "scores_per_item": spi},
+        "per_game_launches_ms": ms_g, "cuda_graph_of_per_game_ms": ms_c,
+        "speedup_vs_per_game": ms_g / ms_p, "speedup_vs_graph": ms_c / ms_p,
+        "roofline": {"bound": "hbm", "kernel": "fsi_batch_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None},
+        "clocks": clocks.summary(),
+        "gpu_launches": args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -320,7 +382,10 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
-        run_ours(args, rank, world, local_rank)
+        if args.workload == "uneven_1024":
+            run_uneven(args, rank, world, local_rank)
+        else:
+            run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

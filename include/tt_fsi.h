@@ -189,6 +189,23 @@ tt_fsi_status tt_fsi_batch_set_wait_limit(tt_fsi_batch batch, long long polls, i
 tt_fsi_status tt_fsi_batch_check(tt_fsi_batch batch, struct CUstream_st *stream);
 
 /*
+ * BF16 GEMM on the tcgen05 tensor cores (the building block of the student
+ * explainer; no counterpart in the paper's method, which has no learned part):
+ *   Z = A . B^T (+ bias) (* gelu'(dgelu_z) elementwise),  FP32 accumulation,
+ *   A [M, K] and B [N, K] row-major BF16 device arrays (lda, ldb multiples of
+ *   8 elements, >= K; 16-byte aligned), bias [N] FP32 or NULL,
+ *   dgelu_z [M, N] (leading dim ldz) FP32 pre-activations or NULL.
+ * Outputs, each optional (NULL): Cf [M, N] FP32 = Z; Cb [M, N] BF16 =
+ * act(Z); Ct [N, M] BF16 = act(Z)^T; act = identity (act = 0) or GELU (1).
+ * err_dev: a device int that the kernel ORs 1 into if a tensor-core wait
+ * timed out.  Asynchronous on `stream`.
+ */
+tt_fsi_status tt_fsi_gemm_bf16(const void *A, int lda, const void *B, int ldb, int M, int N, int K,
+                               const float *bias, int act, const float *dgelu_z, int ldz, float *Cf,
+                               int ldcf, void *Cb, int ldcb, void *Ct, int ldct, int *err_dev,
+                               struct CUstream_st *stream);
+
+/*
  * Masked-model games.  A GELU MLP f: R^d -> R^h1 -> R^h2 -> R,
  *   f(z) = W3 gelu(W2 gelu(W1 z + b1) + b2) + b3,  gelu(u) = u/2 (1 + erf(u/sqrt 2)),
  * with row-major float64 device weights W1 [h1, d], W2 [h2, h1], W3 [h2] and

@@ -1,0 +1,253 @@
+// BF16 x BF16 -> FP32 GEMM on the 5th-generation tensor cores of sm_103a
+// (tcgen05.mma, accumulators in tensor memory), with fused epilogues.
+//
+//   C[M, N] = A[M, K] . B[N, K]^T      (both operands K-major, row-major in HBM)
+//
+// One CTA (4 warps) computes a 128 x BN tile.  Operand tiles of 128 x 64
+// bf16 are staged in shared memory in the 128-byte swizzled K-major layout
+// (row r at r * 128 bytes, its 16-byte chunk c at chunk c ^ (r & 7)), two
+// stages deep: cp.async fills stage s + 1 while the tensor cores read stage
+// s.  One thread issues four 128 x BN x 16 MMAs per stage and commits them to
+// an mbarrier; every wait on an mbarrier is bounded and, when it runs out,
+// records an error, drains and returns.  The epilogue reads the accumulator
+// rows back with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile rows
+// 32w..32w+31) and applies bias, GELU or a GELU-derivative factor, writing
+// FP32 and/or BF16 outputs, optionally also transposed.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ttfsi_gemm {
+
+constexpr int BM = 128;
+constexpr int BN = 128;
+constexpr int BK = 64;
+constexpr int THREADS = 128;
+constexpr int STAGES = 2;
+constexpr int TILE_BYTES = BM * BK * 2;  // 16 KB per operand tile
+constexpr int SMEM_BYTES = STAGES * 2 * TILE_BYTES + 1024;
+constexpr long long WAIT_LIMIT = 20000000;  // mbarrier polls before giving up
+
+enum : int { kErrGemmTimeout = 1 };
+
+struct GemmArgs {
+    const __nv_bfloat16 *A;
+    const __nv_bfloat16 *B;
+    int lda, ldb;
+    int M, N, K;
+    const float *bias;         // [N] or null
+    int act;                   // 0: none, 1: GELU
+    const float *dgelu_z;      // [M, N] pre-activations: multiply by gelu'(z), or null
+    int ldz;
+    float *Cf;                 // FP32 result (before the activation), or null
+    int ldcf;
+    __nv_bfloat16 *Cb;         // BF16 result (after the activation), or null
+    int ldcb;
+    __nv_bfloat16 *Ct;         // BF16 result transposed ([N, M]), or null
+    int ldct;
+    int *err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: 128-byte swizzle, K-major, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;              // leading byte offset (unused by swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+    d |= (uint64_t)1 << 46;              // version
+    d |= (uint64_t)2 << 61;              // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulate, BF16 A and B, both
+// K-major, M = 128, N = BN.
+__host__ __device__ constexpr uint32_t instr_desc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+// Bounded wait for phase `parity` of the mbarrier; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (long long i = 0; i < WAIT_LIMIT; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
+    const int n = valid ? 16 : 0;  // 0 source bytes: the 16 destination bytes are zero-filled
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+
+__device__ __forceinline__ float gelu_grad_f(float z) {
+    // d/dz [z Phi(z)] = Phi(z) + z phi(z)
+    const float cdf = 0.5f * (1.0f + erff(z * 0.70710678118654752f));
+    const float pdf = 0.39894228040143268f * __expf(-0.5f * z * z);
+    return cdf + z * pdf;
+}
+
+// Fills one 128 x 64 operand tile (rows r0.., columns k0..) into the swizzled
+// layout; rows >= rows_valid or columns >= K are zero.
+__device__ __forceinline__ void load_tile(uint32_t tile, const __nv_bfloat16 *G, int ld, int r0, int rows_valid,
+                                          int k0, int K) {
+    for (int i = threadIdx.x; i < BM * 8; i += THREADS) {
+        const int r = i >> 3, c = i & 7;
+        const int gr = r0 + r, gk = k0 + c * 8;
+        const bool ok = (gr < rows_valid) && (gk < K);
+        const __nv_bfloat16 *src = ok ? G + (long long)gr * ld + gk : G;
+        cp_async16(tile + r * 128 + ((c ^ (r & 7)) << 4), src, ok);
+    }
+}
+
+__global__ void __launch_bounds__(THREADS) gemm_bf16_tcgen05(GemmArgs a) {
+    extern __shared__ __align__(1024) unsigned char gsm_raw[];
+    // 1024-byte alignment of the operand tiles (the swizzle is address based)
+    const uint32_t raw = smem_u32(gsm_raw);
+    const uint32_t base = (raw + 1023) & ~1023u;
+    __shared__ __align__(8) uint64_t mbar[STAGES];
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int s_fail;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int nk = (a.K + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(smem_u32(&mbar[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+    const uint32_t idesc = instr_desc_bf16(BM, BN);
+
+    auto tileA = [&](int s) { return base + (uint32_t)(s * 2) * TILE_BYTES; };
+    auto tileB = [&](int s) { return base + (uint32_t)(s * 2 + 1) * TILE_BYTES; };
+
+    uint32_t phase_bits = 0, issued_bits = 0;  // bit s: parity to wait for / MMAs pending on stage s
+    bool fail = false;
+
+    // prologue: stage 0
+    load_tile(tileA(0), a.A, a.lda, m0, a.M, 0, a.K);
+    load_tile(tileB(0), a.B, a.ldb, n0, a.N, 0, a.K);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+
+    for (int kb = 0; kb < nk && !fail; ++kb) {
+        const int s = kb & 1, sn = s ^ 1;
+        // prefetch the next stage once the MMAs that last read it are done
+        if (kb + 1 < nk) {
+            if ((issued_bits >> sn) & 1u) {
+                if (!mbar_wait(smem_u32(&mbar[sn]), (phase_bits >> sn) & 1u)) fail = true;
+                phase_bits ^= 1u << sn;
+                issued_bits &= ~(1u << sn);
+            }
+            if (!fail) {
+                load_tile(tileA(sn), a.A, a.lda, m0, a.M, (kb + 1) * BK, a.K);
+                load_tile(tileB(sn), a.B, a.ldb, n0, a.N, (kb + 1) * BK, a.K);
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        // the current stage's bytes are in shared memory; make them visible to
+        // the tensor cores (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        fail = __syncthreads_or(fail ? 1 : 0) != 0;  // one decision for the whole CTA
+        if (fail) break;
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int kmax = min(BK, a.K - kb * BK);
+            for (int k16 = 0; k16 * 16 < kmax; ++k16) {
+                const uint64_t da = smem_desc(tileA(s) + k16 * 32);
+                const uint64_t db = smem_desc(tileB(s) + k16 * 32);
+                mma_bf16(tmem, da, db, idesc, (kb > 0 || k16 > 0) ? 1u : 0u);
+            }
+            mma_commit(smem_u32(&mbar[s]));
+        }
+        issued_bits |= 1u << s;
+    }
+    // wait for the last MMAs
+    for (int s = 0; s < STAGES; ++s)
+        if ((issued_bits >> s) & 1u) {
+            if (!mbar_wait(smem_u32(&mbar[s]), (phase_bits >> s) & 1u)) fail = true;
+            phase_bits ^= 1u << s;
+        }
+    if (fail) atomicOr(&s_fail, 1);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    if (!s_fail) {
+        // epilogue: rows m0 + 32 * warp + lane, 16 columns at a time
+        const int row = m0 + 32 * warp + lane;
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row >= a.M) continue;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int col = n0 + c0 + j;
+                if (col >= a.N) continue;
+                float z = __uint_as_float(r[j]);
+                if (a.bias) z += a.bias[col];
+                if (a.dgelu_z) z *= gelu_grad_f(a.dgelu_z[(long long)row * a.ldz + col]);
+                if (a.Cf) a.Cf[(long long)row * a.ldcf + col] = z;
+                const float y = (a.act == 1) ? gelu_f(z) : z;
+                const __nv_bfloat16 yb = __float2bfloat16_rn(y);
+                if (a.Cb) a.Cb[(long long)row * a.ldcb + col] = yb;
+                if (a.Ct) a.Ct[(long long)col * a.ldct + row] = yb;
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicOr(a.err, kErrGemmTimeout);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+}
+
+}  // namespace ttfsi_gemm
