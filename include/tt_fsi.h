@@ -206,15 +206,76 @@ tt_fsi_status tt_fsi_gemm_bf16(const void *A, int lda, const void *B, int ldb, i
                                struct CUstream_st *stream);
 
 /*
+ * Amortised explainer ("student").  No counterpart in the paper's method:
+ * a GELU MLP x [d] -> H -> H -> n_out maps an instance straight to its FSI
+ * scores, trained on (x, exact FSI of v_x) pairs.  Every GEMM of its forward
+ * and backward passes runs on tt_fsi_gemm_bf16 (BF16 operands, FP32
+ * accumulation); master weights and Adam state are FP32.  Its raw outputs
+ * are projected onto the efficiency constraint: phi(empty) = v_empty and
+ * the other n_out - 1 scores are shifted equally so that they sum to
+ * target[b] = v_b(N) - v_empty.
+ *
+ * params layout (FP32, host): W1 [H, d], b1 [H], W2 [H, H], b2 [H],
+ * W3 [n_out, H], b3 [n_out], concatenated.  d and H multiples of 8.
+ * All *_dev arrays are FP32 device memory: x [B, d], labels [B, n_out],
+ * target [B], phi [B, n_out]; loss_dev a device scalar (mean squared error
+ * of the projected outputs) or NULL.  B <= max_batch.
+ */
+typedef struct tt_fsi_student_s *tt_fsi_student;
+
+tt_fsi_status tt_fsi_student_create(int d, int hidden, int n_out, int max_batch, const float *params_host,
+                                    tt_fsi_student *out);
+void tt_fsi_student_destroy(tt_fsi_student s);
+int64_t tt_fsi_student_num_params(tt_fsi_student s);
+/* Adam hyper-parameters (defaults lr 1e-3, betas 0.9 / 0.999, eps 1e-8). */
+tt_fsi_status tt_fsi_student_set_adam(tt_fsi_student s, float lr, float beta1, float beta2, float eps);
+/* Forward, projection, loss and backward: gradients into the student's
+ * gradient buffer (read with tt_fsi_student_get_grads), weights unchanged. */
+tt_fsi_status tt_fsi_student_gradients(tt_fsi_student s, const float *x_dev, const float *labels_dev,
+                                       const float *target_dev, float v_empty, int B, float *loss_dev,
+                                       struct CUstream_st *stream);
+/* tt_fsi_student_gradients followed by one fused Adam step. */
+tt_fsi_status tt_fsi_student_train_step(tt_fsi_student s, const float *x_dev, const float *labels_dev,
+                                        const float *target_dev, float v_empty, int B, float *loss_dev,
+                                        struct CUstream_st *stream);
+/* Projected scores of B instances into phi_dev. */
+tt_fsi_status tt_fsi_student_predict(tt_fsi_student s, const float *x_dev, const float *target_dev,
+                                     float v_empty, int B, float *phi_dev, struct CUstream_st *stream);
+/* Checkpoint / resume: FP32 parameters, Adam moments and step count (host
+ * arrays of tt_fsi_student_num_params floats; any pointer may be NULL). */
+tt_fsi_status tt_fsi_student_get_state(tt_fsi_student s, float *params_host, float *adam_m_host,
+                                       float *adam_v_host, int64_t *step);
+tt_fsi_status tt_fsi_student_set_state(tt_fsi_student s, const float *params_host, const float *adam_m_host,
+                                       const float *adam_v_host, int64_t step);
+tt_fsi_status tt_fsi_student_get_grads(tt_fsi_student s, float *grads_host);
+/* Waits for the stream; TT_FSI_ERR_TIMEOUT if a tensor-core wait gave up. */
+tt_fsi_status tt_fsi_student_check(tt_fsi_student s, struct CUstream_st *stream);
+
+/*
+ * Residual spot check of scores as an order-l surrogate (the fitted model of
+ * Eq. fsi_wls): for instance b and sampled coalition T = coal[b, k],
+ * g(T) = sum over scores q with score_masks[q] subset of T of phi[b, q], and
+ * resid[b] = sqrt(mean_k (g(T) - vcoal[b, k])^2).  coal [B, K] and
+ * score_masks [n_out] are uint32 coalition masks (d <= 32), vcoal [B, K]
+ * the game's values at those coalitions; FP32 device arrays.
+ */
+tt_fsi_status tt_fsi_surrogate_residual(const float *phi_dev, int B, int n_out, const unsigned *score_masks_dev,
+                                        const unsigned *coal_dev, const float *vcoal_dev, int K, float *resid_dev,
+                                        struct CUstream_st *stream);
+
+/*
  * Masked-model games.  A GELU MLP f: R^d -> R^h1 -> R^h2 -> R,
  *   f(z) = W3 gelu(W2 gelu(W1 z + b1) + b2) + b3,  gelu(u) = u/2 (1 + erf(u/sqrt 2)),
  * with row-major float64 device weights W1 [h1, d], W2 [h2, h1], W3 [h2] and
  * biases b1 [h1], b2 [h2], b3 (host scalar); 1 <= d <= 30, 1 <= h1, h2 <= 256.
+ * The float32 paths use the float32 copies W1f ... W3f of the same arrays
+ * (required for them).
  */
 typedef struct {
     int d, h1, h2;
     const double *W1, *b1, *W2, *b2, *W3;
     double b3;
+    const float *W1f, *b1f, *W2f, *b2f, *W3f;
 } tt_fsi_mlp;
 
 /*
@@ -229,6 +290,16 @@ typedef struct {
 tt_fsi_status tt_fsi_masked_game(const tt_fsi_mlp *model, const double *x_dev,
                                  const double *baseline_dev, int64_t B, void *v_dev, int out_f32,
                                  struct CUstream_st *stream);
+
+/*
+ * The same value function at K given coalitions per instance:
+ * out[b, k] = f(z), z_i = x[b, i] if bit i of coal[b, k] is set, else
+ * baseline[i]; coal [B, K] uint32 masks (d <= 32), out [B, K] FP32
+ * (computed in FP32).  Asynchronous on `stream`.
+ */
+tt_fsi_status tt_fsi_masked_game_sampled(const tt_fsi_mlp *model, const double *x_dev,
+                                         const double *baseline_dev, int64_t B, const unsigned *coal_dev,
+                                         int K, float *out_dev, struct CUstream_st *stream);
 
 /*
  * Waits for the plan's work on `stream`, then reads and clears the plan's

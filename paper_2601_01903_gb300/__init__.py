@@ -125,7 +125,9 @@ def fsi(v, d: int, ell: int, arith: str = "exact"):
 class _Mlp(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("h1", ctypes.c_int), ("h2", ctypes.c_int),
                 ("W1", ctypes.c_void_p), ("b1", ctypes.c_void_p), ("W2", ctypes.c_void_p),
-                ("b2", ctypes.c_void_p), ("W3", ctypes.c_void_p), ("b3", ctypes.c_double)]
+                ("b2", ctypes.c_void_p), ("W3", ctypes.c_void_p), ("b3", ctypes.c_double),
+                ("W1f", ctypes.c_void_p), ("b1f", ctypes.c_void_p), ("W2f", ctypes.c_void_p),
+                ("b2f", ctypes.c_void_p), ("W3f", ctypes.c_void_p)]
 
 
 class DeviceMLP:
@@ -141,8 +143,10 @@ class DeviceMLP:
         self.b3 = float(np.asarray(mlp.b3).reshape(-1)[0])
         self.h1, self.d = self.W1.shape
         self.h2 = self.W2.shape[0]
+        self._f = [t.float().contiguous() for t in (self.W1, self.b1, self.W2, self.b2, self.W3)]
         self._s = _Mlp(self.d, self.h1, self.h2, self.W1.data_ptr(), self.b1.data_ptr(),
-                       self.W2.data_ptr(), self.b2.data_ptr(), self.W3.data_ptr(), self.b3)
+                       self.W2.data_ptr(), self.b2.data_ptr(), self.W3.data_ptr(), self.b3,
+                       *[t.data_ptr() for t in self._f])
 
     @property
     def struct(self):

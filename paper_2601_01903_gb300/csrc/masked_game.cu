@@ -42,6 +42,23 @@ struct Args {
     void *v;
     int d, h1, h2;
     long long game0;
+    const float *W1f, *b1f, *W2f, *b2f, *W3f;
+};
+
+// Weights in the arithmetic of the instantiation (float64 or float32 copies).
+template <typename T>
+struct W;
+template <>
+struct W<double> {
+    static __device__ __forceinline__ const double *w2(const Args &a) { return a.W2; }
+    static __device__ __forceinline__ double b2(const Args &a, int j) { return a.b2[j]; }
+    static __device__ __forceinline__ double w3(const Args &a, int j) { return a.W3[j]; }
+};
+template <>
+struct W<float> {
+    static __device__ __forceinline__ const float *w2(const Args &a) { return a.W2f; }
+    static __device__ __forceinline__ float b2(const Args &a, int j) { return a.b2f[j]; }
+    static __device__ __forceinline__ float w3(const Args &a, int j) { return a.W3f[j]; }
 };
 
 template <typename T>
@@ -83,10 +100,10 @@ __global__ void __launch_bounds__(THREADS) masked_game_kernel(Args a) {
     if (c < nc) {
         const T *row = pre + c * ld;
         for (int j = half; j < a.h2; j += 2) {
-            const double *w = a.W2 + (long long)j * a.h1;
-            T acc = (T)a.b2[j];
-            for (int i = 0; i < a.h1; ++i) acc += (T)__ldg(w + i) * row[i];
-            acc3 += (T)a.W3[j] * gelu<T>(acc);
+            const T *w = W<T>::w2(a) + (long long)j * a.h1;
+            T acc = W<T>::b2(a, j);
+            for (int i = 0; i < a.h1; ++i) acc += __ldg(w + i) * row[i];
+            acc3 += W<T>::w3(a, j) * gelu<T>(acc);
         }
     }
     part[tid] = acc3;
@@ -111,8 +128,10 @@ extern "C" tt_fsi_status tt_fsi_masked_game(const tt_fsi_mlp *model, const doubl
     if (model->d < 1 || model->d > 30 || model->h1 < 1 || model->h2 < 1 || model->h1 > MAX_H ||
         model->h2 > MAX_H)
         return TT_FSI_ERR_INVALID_ARG;
+    if (out_f32 && (!model->W2f || !model->b2f || !model->W3f)) return TT_FSI_ERR_INVALID_ARG;
     Args a{model->W1, model->b1, model->W2, model->b2, model->W3, model->b3,
-           x_dev, baseline_dev, v_dev, model->d, model->h1, model->h2, 0};
+           x_dev, baseline_dev, v_dev, model->d, model->h1, model->h2, 0,
+           model->W1f, model->b1f, model->W2f, model->b2f, model->W3f};
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int g = model->d < G ? model->d : G;
     const size_t elem = out_f32 ? sizeof(float) : sizeof(double);
@@ -136,4 +155,75 @@ extern "C" tt_fsi_status tt_fsi_masked_game(const tt_fsi_mlp *model, const doubl
         if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TT_FSI_ERR_NO_MEMORY : TT_FSI_ERR_CUDA;
     }
     return TT_FSI_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Value function at sampled coalitions (FP32): one warp per (instance,
+// coalition); layer-1 and layer-2 units are spread over the lanes, layer 3 is
+// a warp reduction.  Used by the student's residual spot check.
+// ----------------------------------------------------------------------------
+namespace ttfsi_mg {
+
+constexpr int SW = 8;  // warps per block
+
+__global__ void __launch_bounds__(32 * SW) masked_game_sampled_kernel(Args a, const unsigned *coal, int K, long long total,
+                                                                      float *out) {
+    extern __shared__ __align__(16) unsigned char smem_s[];
+    float *h1 = reinterpret_cast<float *>(smem_s) + (threadIdx.x >> 5) * (a.h1 + 64);
+    const int lane = threadIdx.x & 31;
+    for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < total;
+         w += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const long long b = w / K;
+        const unsigned T = coal[w];
+        const double *x = a.x + b * a.d;
+        // the instance's features and the baseline, converted once per coalition
+        float *zf = h1 + a.h1;
+        for (int i = lane; i < a.d; i += 32) {
+            zf[i] = (float)x[i];
+            zf[32 + i] = (float)a.base[i];
+        }
+        __syncwarp();
+        for (int j = lane; j < a.h1; j += 32) {
+            float acc = a.b1f[j];
+            for (int i = 0; i < a.d; ++i) acc += a.W1f[(long long)j * a.d + i] * zf[((T >> i) & 1u) ? i : 32 + i];
+            h1[j] = gelu<float>(acc);
+        }
+        __syncwarp();
+        float acc3 = 0.f;
+        for (int j = lane; j < a.h2; j += 32) {
+            float acc = a.b2f[j];
+            const float *w = a.W2f + (long long)j * a.h1;
+            for (int i = 0; i < a.h1; ++i) acc += __ldg(w + i) * h1[i];
+            acc3 += a.W3f[j] * gelu<float>(acc);
+        }
+        for (int o = 16; o > 0; o >>= 1) acc3 += __shfl_xor_sync(0xffffffffu, acc3, o);
+        if (lane == 0) out[w] = acc3 + (float)a.b3;
+        __syncwarp();
+    }
+}
+
+}  // namespace ttfsi_mg
+
+extern "C" tt_fsi_status tt_fsi_masked_game_sampled(const tt_fsi_mlp *model, const double *x_dev,
+                                                   const double *baseline_dev, int64_t B, const unsigned *coal_dev,
+                                                   int K, float *out_dev, struct CUstream_st *stream) {
+    using namespace ttfsi_mg;
+    if (!model || B < 0 || K < 1) return TT_FSI_ERR_INVALID_ARG;
+    if (B == 0) return TT_FSI_OK;
+    if (!x_dev || !baseline_dev || !coal_dev || !out_dev || !model->W1 || !model->b1 || !model->W2 ||
+        !model->b2 || !model->W3)
+        return TT_FSI_ERR_INVALID_ARG;
+    if (model->d < 1 || model->d > 32 || model->h1 < 1 || model->h2 < 1 || model->h1 > MAX_H || model->h2 > MAX_H)
+        return TT_FSI_ERR_INVALID_ARG;
+    if (!model->W1f || !model->b1f || !model->W2f || !model->b2f || !model->W3f) return TT_FSI_ERR_INVALID_ARG;
+    Args a{model->W1, model->b1, model->W2, model->b2, model->W3, model->b3,
+           x_dev, baseline_dev, nullptr, model->d, model->h1, model->h2, 0,
+           model->W1f, model->b1f, model->W2f, model->b2f, model->W3f};
+    const long long total = B * (long long)K;
+    long long blocks = (total + SW - 1) / SW;
+    if (blocks > 65535LL * 16) blocks = 65535LL * 16;
+    const size_t smem = (size_t)SW * (model->h1 + 64) * sizeof(float);
+    masked_game_sampled_kernel<<<(unsigned)blocks, 32 * SW, smem, reinterpret_cast<cudaStream_t>(stream)>>>(
+        a, coal_dev, K, total, out_dev);
+    return cudaGetLastError() == cudaSuccess ? TT_FSI_OK : TT_FSI_ERR_CUDA;
 }

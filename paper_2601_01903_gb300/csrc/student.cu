@@ -63,3 +63,468 @@ extern "C" tt_fsi_status tt_fsi_gemm_bf16(const void *A, int lda, const void *B,
     a.err = err_dev;
     return gemm_launch(a, reinterpret_cast<cudaStream_t>(stream));
 }
+
+// ============================================================================
+// Student network d -> H -> H -> n_out (GELU), BF16 operands on the tensor
+// cores, FP32 master weights and Adam state, output projected onto the
+// efficiency constraint.
+// ============================================================================
+#include <cmath>
+#include <new>
+#include <vector>
+
+namespace ttfsi_student {
+
+using bf16 = __nv_bfloat16;
+constexpr int kErrTimeout = 1;
+
+__global__ void x_to_bf16_kernel(const float *x, int B, int d, bf16 *xb, bf16 *xbt, int ldt) {
+    const long long n = (long long)B * d;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(i / d), j = (int)(i - (long long)b * d);
+        const bf16 v = __float2bfloat16_rn(x[i]);
+        xb[i] = v;
+        if (xbt) xbt[(long long)j * ldt + b] = v;
+    }
+}
+
+// BF16 copies of the FP32 weights: W [rows, cols] -> Wb [rows_pad, cols]
+// (rows >= rows zero) and optionally Wt [cols, ldt] = W^T (columns >= rows zero).
+__global__ void weights_to_bf16_kernel(const float *W, int rows, int cols, int rows_pad, bf16 *Wb, bf16 *Wt, int ldt) {
+    const long long n = (long long)rows_pad * cols;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / cols), c = (int)(i - (long long)r * cols);
+        const float w = (r < rows) ? W[(long long)r * cols + c] : 0.0f;
+        const bf16 v = __float2bfloat16_rn(w);
+        Wb[i] = v;
+        if (Wt) Wt[(long long)c * ldt + r] = v;
+    }
+}
+
+// Projection onto sum_{S != empty} phi(S) = target, phi(empty) = v_empty, then
+// (if labels are given) the squared-error loss and its gradient with respect
+// to the raw outputs: dL/dY = P (2 (phi_p - phi) / (B n_out)), P = I - 11^T/(n_out-1)
+// on the non-empty coordinates, 0 on the empty one.  One warp per instance.
+__global__ void project_loss_kernel(const float *Y, int B, int n_out, const float *target, float v_empty, float *phi,
+                                    const float *labels, float *loss_rows, float *dYf, bf16 *dYb, int ld_dyb, bf16 *dYt,
+                                    int ld_dyt) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= B) return;
+    const float *y = Y + (long long)warp * n_out;
+    float s = 0.f;
+    for (int k = 1 + lane; k < n_out; k += 32) s += y[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const float shift = (target[warp] - s) / (float)(n_out - 1);
+    float loss = 0.f, gsum = 0.f;
+    const float scale = 2.0f / ((float)B * (float)n_out);
+    for (int k = lane; k < n_out; k += 32) {
+        const float p = (k == 0) ? v_empty : y[k] + shift;
+        if (phi) phi[(long long)warp * n_out + k] = p;
+        if (labels) {
+            const float e = p - labels[(long long)warp * n_out + k];
+            loss += e * e;
+            if (k > 0) gsum += scale * e;
+        }
+    }
+    if (!labels) return;
+    for (int o = 16; o > 0; o >>= 1) {
+        loss += __shfl_xor_sync(0xffffffffu, loss, o);
+        gsum += __shfl_xor_sync(0xffffffffu, gsum, o);
+    }
+    if (lane == 0) loss_rows[warp] = loss;
+    const float gmean = gsum / (float)(n_out - 1);
+    for (int k = lane; k < ld_dyb; k += 32) {
+        float g = 0.f;
+        if (k > 0 && k < n_out) {
+            const float p = y[k] + shift;
+            g = scale * (p - labels[(long long)warp * n_out + k]) - gmean;
+        }
+        if (k < n_out) dYf[(long long)warp * n_out + k] = g;
+        const bf16 gb = __float2bfloat16_rn(g);
+        dYb[(long long)warp * ld_dyb + k] = gb;
+        if (k < n_out) dYt[(long long)k * ld_dyt + warp] = gb;
+    }
+}
+
+// Column sums of an FP32 [M, N] matrix, one thread per column, fixed order.
+__global__ void colsum_kernel(const float *X, int M, int N, float *out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    float s = 0.f;
+    for (int r = 0; r < M; ++r) s += X[(long long)r * N + c];
+    out[c] = s;
+}
+
+// Sum of the per-instance losses, one block, fixed order.
+__global__ void sum_kernel(const float *x, int n, float scale, float *out) {
+    __shared__ float red[256];
+    float s = 0.f;
+    for (int i = threadIdx.x; i < n; i += 256) s += x[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0] * scale;
+}
+
+// Adam (Kingma & Ba): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+// p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps), over a flat buffer.
+__global__ void adam_kernel(float *p, float *m, float *v, const float *g, long long n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// Surrogate residual of each instance on its sampled coalitions:
+// g(T) = sum over scores S subset of T of phi(S);
+// r = sqrt(mean_k (g(T_k) - v(T_k))^2).  One warp per instance.
+__global__ void residual_kernel(const float *phi, int B, int n_out, const unsigned *masks, const unsigned *coal,
+                                const float *vcoal, int K, float *resid) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= B) return;
+    float acc = 0.f;
+    for (int k = lane; k < K; k += 32) {
+        const unsigned T = coal[(long long)warp * K + k];
+        float g = 0.f;
+        for (int q = 0; q < n_out; ++q)
+            if ((masks[q] & T) == masks[q]) g += phi[(long long)warp * n_out + q];
+        const float e = g - vcoal[(long long)warp * K + k];
+        acc += e * e;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) resid[warp] = sqrtf(acc / (float)K);
+}
+
+int grid_for(long long n) {
+    long long g = (n + 255) / 256;
+    if (g > 4096) g = 4096;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace ttfsi_student
+
+struct tt_fsi_student_s {
+    int d = 0, H = 0, n_out = 0, n_pad = 0, max_batch = 0, ldB = 0;
+    long long n_params = 0;
+    long long off_W1 = 0, off_b1 = 0, off_W2 = 0, off_b2 = 0, off_W3 = 0, off_b3 = 0;
+    float *params = nullptr, *m = nullptr, *v = nullptr, *grads = nullptr;
+    __nv_bfloat16 *W1b = nullptr, *W2b = nullptr, *W2bT = nullptr, *W3b = nullptr, *W3bT = nullptr;
+    __nv_bfloat16 *Xb = nullptr, *XbT = nullptr, *A1 = nullptr, *A1T = nullptr, *A2 = nullptr, *A2T = nullptr;
+    __nv_bfloat16 *dYb = nullptr, *dYt = nullptr, *dH2 = nullptr, *dH2T = nullptr, *dH1T = nullptr;
+    float *Z1 = nullptr, *Z2 = nullptr, *Y = nullptr, *dYf = nullptr, *dH2f = nullptr, *dH1f = nullptr;
+    float *loss_rows = nullptr;
+    int *err = nullptr;
+    float lr = 1e-3f, beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
+    long long step = 0;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+using ttfsi_student::bf16;
+
+template <typename T>
+cudaError_t st_alloc(tt_fsi_student_s *s, T **p, size_t count) {
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T) + 16);
+    if (e == cudaSuccess) {
+        s->allocs.push_back(*p);
+        e = cudaMemset(*p, 0, count * sizeof(T) + 16);
+    }
+    return e;
+}
+
+tt_fsi_status gemm(const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N, int K, const float *bias, int act,
+                   const float *dz, int ldz, float *Cf, int ldcf, bf16 *Cb, int ldcb, bf16 *Ct, int ldct, int *err,
+                   cudaStream_t st) {
+    ttfsi_gemm::GemmArgs a{};
+    a.A = A;
+    a.B = B;
+    a.lda = lda;
+    a.ldb = ldb;
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.bias = bias;
+    a.act = act;
+    a.dgelu_z = dz;
+    a.ldz = ldz;
+    a.Cf = Cf;
+    a.ldcf = ldcf;
+    a.Cb = Cb;
+    a.ldcb = ldcb;
+    a.Ct = Ct;
+    a.ldct = ldct;
+    a.err = err;
+    return gemm_launch(a, st);
+}
+
+tt_fsi_status refresh_bf16(tt_fsi_student_s *s, cudaStream_t st) {
+    using namespace ttfsi_student;
+    weights_to_bf16_kernel<<<grid_for((long long)s->H * s->d), 256, 0, st>>>(s->params + s->off_W1, s->H, s->d, s->H,
+                                                                           s->W1b, nullptr, 0);
+    weights_to_bf16_kernel<<<grid_for((long long)s->H * s->H), 256, 0, st>>>(s->params + s->off_W2, s->H, s->H, s->H,
+                                                                           s->W2b, s->W2bT, s->H);
+    weights_to_bf16_kernel<<<grid_for((long long)s->n_pad * s->H), 256, 0, st>>>(
+        s->params + s->off_W3, s->n_out, s->H, s->n_pad, s->W3b, s->W3bT, s->n_pad);
+    return st_status(cudaGetLastError());
+}
+
+// Forward pass into s->Y (raw outputs); `train` also keeps what the backward
+// pass needs (transposed activations).
+tt_fsi_status forward(tt_fsi_student_s *s, const float *x, int B, bool train, cudaStream_t st) {
+    using namespace ttfsi_student;
+    x_to_bf16_kernel<<<grid_for((long long)B * s->d), 256, 0, st>>>(x, B, s->d, s->Xb, train ? s->XbT : nullptr, s->ldB);
+    tt_fsi_status r = st_status(cudaGetLastError());
+    if (r != TT_FSI_OK) return r;
+    const float *P = s->params;
+    r = gemm(s->Xb, s->d, s->W1b, s->d, B, s->H, s->d, P + s->off_b1, 1, nullptr, 0, s->Z1, s->H, s->A1, s->H,
+             train ? s->A1T : nullptr, s->ldB, s->err, st);
+    if (r != TT_FSI_OK) return r;
+    r = gemm(s->A1, s->H, s->W2b, s->H, B, s->H, s->H, P + s->off_b2, 1, nullptr, 0, s->Z2, s->H, s->A2, s->H,
+             train ? s->A2T : nullptr, s->ldB, s->err, st);
+    if (r != TT_FSI_OK) return r;
+    return gemm(s->A2, s->H, s->W3b, s->H, B, s->n_out, s->H, P + s->off_b3, 0, nullptr, 0, s->Y, s->n_out, nullptr, 0,
+                nullptr, 0, s->err, st);
+}
+
+// Gradients of the mean squared error of the projected outputs into s->grads.
+tt_fsi_status backward(tt_fsi_student_s *s, const float *labels, const float *target, float v_empty, int B,
+                       float *loss_dev, cudaStream_t st) {
+    using namespace ttfsi_student;
+    const int warps_per_block = 8;
+    project_loss_kernel<<<(B + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
+        s->Y, B, s->n_out, target, v_empty, nullptr, labels, s->loss_rows, s->dYf, s->dYb, s->n_pad, s->dYt, s->ldB);
+    tt_fsi_status r = st_status(cudaGetLastError());
+    if (r != TT_FSI_OK) return r;
+    if (loss_dev) sum_kernel<<<1, 256, 0, st>>>(s->loss_rows, B, 1.0f / ((float)B * s->n_out), loss_dev);
+    float *G = s->grads;
+    // layer 3
+    r = gemm(s->dYt, s->ldB, s->A2T, s->ldB, s->n_out, s->H, B, nullptr, 0, nullptr, 0, G + s->off_W3, s->H, nullptr, 0,
+             nullptr, 0, s->err, st);
+    if (r != TT_FSI_OK) return r;
+    colsum_kernel<<<(s->n_out + 127) / 128, 128, 0, st>>>(s->dYf, B, s->n_out, G + s->off_b3);
+    r = gemm(s->dYb, s->n_pad, s->W3bT, s->n_pad, B, s->H, s->n_pad, nullptr, 0, s->Z2, s->H, s->dH2f, s->H, s->dH2,
+             s->H, s->dH2T, s->ldB, s->err, st);
+    if (r != TT_FSI_OK) return r;
+    // layer 2
+    colsum_kernel<<<(s->H + 127) / 128, 128, 0, st>>>(s->dH2f, B, s->H, G + s->off_b2);
+    r = gemm(s->dH2T, s->ldB, s->A1T, s->ldB, s->H, s->H, B, nullptr, 0, nullptr, 0, G + s->off_W2, s->H, nullptr, 0,
+             nullptr, 0, s->err, st);
+    if (r != TT_FSI_OK) return r;
+    r = gemm(s->dH2, s->H, s->W2bT, s->H, B, s->H, s->H, nullptr, 0, s->Z1, s->H, s->dH1f, s->H, nullptr, 0, s->dH1T,
+             s->ldB, s->err, st);
+    if (r != TT_FSI_OK) return r;
+    // layer 1
+    colsum_kernel<<<(s->H + 127) / 128, 128, 0, st>>>(s->dH1f, B, s->H, G + s->off_b1);
+    r = gemm(s->dH1T, s->ldB, s->XbT, s->ldB, s->H, s->d, B, nullptr, 0, nullptr, 0, G + s->off_W1, s->d, nullptr, 0,
+             nullptr, 0, s->err, st);
+    if (r != TT_FSI_OK) return r;
+    return st_status(cudaGetLastError());
+}
+
+void student_free(tt_fsi_student_s *s) {
+    for (void *p : s->allocs) cudaFree(p);
+    s->allocs.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+tt_fsi_status tt_fsi_student_create(int d, int hidden, int n_out, int max_batch, const float *params_host,
+                                    tt_fsi_student *out) {
+    if (!out || !params_host || d < 1 || hidden < 8 || n_out < 2 || max_batch < 1) return TT_FSI_ERR_INVALID_ARG;
+    if ((d % 8) || (hidden % 8)) return TT_FSI_ERR_UNSUPPORTED;  // 16-byte rows of the BF16 operands
+    *out = nullptr;
+    tt_fsi_student_s *s = new (std::nothrow) tt_fsi_student_s();
+    if (!s) return TT_FSI_ERR_NO_MEMORY;
+    s->d = d;
+    s->H = hidden;
+    s->n_out = n_out;
+    s->n_pad = (n_out + 15) / 16 * 16;
+    s->max_batch = max_batch;
+    s->ldB = (max_batch + 7) / 8 * 8;
+    long long o = 0;
+    s->off_W1 = o;
+    o += (long long)hidden * d;
+    s->off_b1 = o;
+    o += hidden;
+    s->off_W2 = o;
+    o += (long long)hidden * hidden;
+    s->off_b2 = o;
+    o += hidden;
+    s->off_W3 = o;
+    o += (long long)n_out * hidden;
+    s->off_b3 = o;
+    o += n_out;
+    s->n_params = o;
+    const size_t Bm = (size_t)s->ldB, H = (size_t)hidden;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto **p, size_t n) {
+        if (e == cudaSuccess) e = st_alloc(s, p, n);
+    };
+    A(&s->params, (size_t)o);
+    A(&s->m, (size_t)o);
+    A(&s->v, (size_t)o);
+    A(&s->grads, (size_t)o);
+    A(&s->W1b, H * d);
+    A(&s->W2b, H * H);
+    A(&s->W2bT, H * H);
+    A(&s->W3b, (size_t)s->n_pad * H);
+    A(&s->W3bT, H * s->n_pad);
+    A(&s->Xb, Bm * d);
+    A(&s->XbT, (size_t)d * Bm);
+    A(&s->A1, Bm * H);
+    A(&s->A1T, H * Bm);
+    A(&s->A2, Bm * H);
+    A(&s->A2T, H * Bm);
+    A(&s->Z1, Bm * H);
+    A(&s->Z2, Bm * H);
+    A(&s->Y, Bm * n_out);
+    A(&s->dYf, Bm * n_out);
+    A(&s->dYb, Bm * s->n_pad);
+    A(&s->dYt, (size_t)s->n_pad * Bm);
+    A(&s->dH2f, Bm * H);
+    A(&s->dH2, Bm * H);
+    A(&s->dH2T, H * Bm);
+    A(&s->dH1f, Bm * H);
+    A(&s->dH1T, H * Bm);
+    A(&s->loss_rows, Bm);
+    A(&s->err, 1);
+    if (e == cudaSuccess) e = cudaMemcpy(s->params, params_host, (size_t)o * sizeof(float), cudaMemcpyHostToDevice);
+    tt_fsi_status r = st_status(e);
+    if (r == TT_FSI_OK) r = refresh_bf16(s, nullptr);
+    if (r == TT_FSI_OK) r = st_status(cudaDeviceSynchronize());
+    if (r != TT_FSI_OK) {
+        student_free(s);
+        delete s;
+        return r;
+    }
+    *out = s;
+    return TT_FSI_OK;
+}
+
+void tt_fsi_student_destroy(tt_fsi_student s) {
+    if (!s) return;
+    cudaDeviceSynchronize();
+    student_free(s);
+    delete s;
+}
+
+int64_t tt_fsi_student_num_params(tt_fsi_student s) { return s ? s->n_params : -1; }
+
+tt_fsi_status tt_fsi_student_set_adam(tt_fsi_student s, float lr, float beta1, float beta2, float eps) {
+    if (!s || !(lr >= 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+        return TT_FSI_ERR_INVALID_ARG;
+    s->lr = lr;
+    s->beta1 = beta1;
+    s->beta2 = beta2;
+    s->eps = eps;
+    return TT_FSI_OK;
+}
+
+tt_fsi_status tt_fsi_student_gradients(tt_fsi_student s, const float *x_dev, const float *labels_dev,
+                                       const float *target_dev, float v_empty, int B, float *loss_dev,
+                                       struct CUstream_st *stream) {
+    if (!s || !x_dev || !labels_dev || !target_dev || B < 1 || B > s->max_batch) return TT_FSI_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    tt_fsi_status r = forward(s, x_dev, B, true, st);
+    if (r == TT_FSI_OK) r = backward(s, labels_dev, target_dev, v_empty, B, loss_dev, st);
+    return r;
+}
+
+tt_fsi_status tt_fsi_student_train_step(tt_fsi_student s, const float *x_dev, const float *labels_dev,
+                                        const float *target_dev, float v_empty, int B, float *loss_dev,
+                                        struct CUstream_st *stream) {
+    tt_fsi_status r = tt_fsi_student_gradients(s, x_dev, labels_dev, target_dev, v_empty, B, loss_dev, stream);
+    if (r != TT_FSI_OK) return r;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    s->step += 1;
+    const float c1 = 1.0f - (float)std::pow((double)s->beta1, (double)s->step);
+    const float c2 = 1.0f - (float)std::pow((double)s->beta2, (double)s->step);
+    ttfsi_student::adam_kernel<<<ttfsi_student::grid_for(s->n_params), 256, 0, st>>>(
+        s->params, s->m, s->v, s->grads, s->n_params, s->lr, s->beta1, s->beta2, s->eps, c1, c2);
+    r = st_status(cudaGetLastError());
+    if (r == TT_FSI_OK) r = refresh_bf16(s, st);
+    return r;
+}
+
+tt_fsi_status tt_fsi_student_predict(tt_fsi_student s, const float *x_dev, const float *target_dev, float v_empty,
+                                     int B, float *phi_dev, struct CUstream_st *stream) {
+    if (!s || !x_dev || !target_dev || !phi_dev || B < 1 || B > s->max_batch) return TT_FSI_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    tt_fsi_status r = forward(s, x_dev, B, false, st);
+    if (r != TT_FSI_OK) return r;
+    ttfsi_student::project_loss_kernel<<<(B + 7) / 8, 256, 0, st>>>(s->Y, B, s->n_out, target_dev, v_empty, phi_dev,
+                                                                  nullptr, nullptr, nullptr, nullptr, 0, nullptr, 0);
+    return st_status(cudaGetLastError());
+}
+
+tt_fsi_status tt_fsi_student_get_state(tt_fsi_student s, float *params_host, float *adam_m_host, float *adam_v_host,
+                                       int64_t *step) {
+    if (!s) return TT_FSI_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)s->n_params * sizeof(float);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && params_host) e = cudaMemcpy(params_host, s->params, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && adam_m_host) e = cudaMemcpy(adam_m_host, s->m, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && adam_v_host) e = cudaMemcpy(adam_v_host, s->v, bytes, cudaMemcpyDeviceToHost);
+    if (step) *step = s->step;
+    return st_status(e);
+}
+
+tt_fsi_status tt_fsi_student_set_state(tt_fsi_student s, const float *params_host, const float *adam_m_host,
+                                       const float *adam_v_host, int64_t step) {
+    if (!s || step < 0) return TT_FSI_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)s->n_params * sizeof(float);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && params_host) e = cudaMemcpy(s->params, params_host, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && adam_m_host) e = cudaMemcpy(s->m, adam_m_host, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && adam_v_host) e = cudaMemcpy(s->v, adam_v_host, bytes, cudaMemcpyHostToDevice);
+    s->step = step;
+    tt_fsi_status r = st_status(e);
+    if (r == TT_FSI_OK) r = refresh_bf16(s, nullptr);
+    if (r == TT_FSI_OK) r = st_status(cudaDeviceSynchronize());
+    return r;
+}
+
+tt_fsi_status tt_fsi_student_get_grads(tt_fsi_student s, float *grads_host) {
+    if (!s || !grads_host) return TT_FSI_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpy(grads_host, s->grads, (size_t)s->n_params * sizeof(float), cudaMemcpyDeviceToHost);
+    return st_status(e);
+}
+
+tt_fsi_status tt_fsi_student_check(tt_fsi_student s, struct CUstream_st *stream) {
+    if (!s) return TT_FSI_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, s->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return st_status(e);
+    return h ? TT_FSI_ERR_TIMEOUT : TT_FSI_OK;
+}
+
+tt_fsi_status tt_fsi_surrogate_residual(const float *phi_dev, int B, int n_out, const unsigned *score_masks_dev,
+                                        const unsigned *coal_dev, const float *vcoal_dev, int K, float *resid_dev,
+                                        struct CUstream_st *stream) {
+    if (B < 0 || n_out < 1 || K < 1) return TT_FSI_ERR_INVALID_ARG;
+    if (B == 0) return TT_FSI_OK;
+    if (!phi_dev || !score_masks_dev || !coal_dev || !vcoal_dev || !resid_dev) return TT_FSI_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    ttfsi_student::residual_kernel<<<(B + 7) / 8, 256, 0, st>>>(phi_dev, B, n_out, score_masks_dev, coal_dev, vcoal_dev,
+                                                              K, resid_dev);
+    return st_status(cudaGetLastError());
+}
+
+}  // extern "C"
