@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--workload", default="mlp_d20_l3_b16",
-                    choices=["mlp_d20_l3_b16", "uneven_1024"],
+                    choices=["mlp_d20_l3_b16", "uneven_1024", "student"],
                     help="mlp_d20_l3_b16: the headline batch; uneven_1024: 1024 Moebius-sparse "
                          "games with d in 10..20 and l in 1..3, one persistent launch vs "
                          "per-game launches vs a CUDA graph of them")
@@ -368,6 +368,90 @@ def run_uneven(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_student(args, rank, world, local_rank):
+    """Amortised explainer: d=16, l=2 (137 scores), teacher 16-128-128-1,
+    x ~ N(0, Sigma) with Sigma_ij = 0.5^|i-j|; 200k training / 10k held-out
+    pairs labelled by the exact path; student 16-1024-1024-137, batch 4096.
+    Reports training throughput (GEMM TFLOP/s), inference instances/s with
+    and without the residual check, the exact path's instances/s, and the
+    student's error against exact FSI on the held-out set."""
+    import numpy as np
+    import torch
+    from paper_2601_01903_gb300 import student as st, synthetic
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    H, BATCH_S, N_TRAIN, N_HELD = 1024, 4096, 200_000, 10_000
+    epochs = max(1, args.steps)
+    ex = st.Explainer(synthetic.workload_student_teacher(), ell=2, hidden=H, batch=BATCH_S)
+    t0 = time.perf_counter()
+    train = ex.dataset(N_TRAIN, first=0)
+    held = ex.dataset(N_HELD, first=N_TRAIN)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    # training (all GEMMs on tcgen05)
+    nb = N_TRAIN // BATCH_S
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+    with ClockSampler(local_rank) as clocks:
+        e0.record(stream)
+        losses = ex.train(train, epochs=epochs, lr=1e-3)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms_train = e0.elapsed_time(e1)
+    steps = epochs * nb
+    d, n_out = 16, ex.n_out
+    flop_fwd = 2 * BATCH_S * (d * H + H * H + H * n_out)
+    flop_step = 3 * flop_fwd  # forward, input gradients, weight gradients
+    tflops = flop_step * steps / (ms_train * 1e-3) / 1e12
+    # held-out error against exact FSI
+    tau = ex.calibrate(held)
+    phi = ex.predict_raw(held.x, held.target).double()
+    lab = held.labels.double()
+    rmse = torch.sqrt(((phi - lab) ** 2).mean()).item()
+    rel = (torch.linalg.norm(phi - lab) / torch.linalg.norm(lab)).item()
+    out, fb = ex.explain(held.x, held.target, first=N_TRAIN)
+    rel_fb = (torch.linalg.norm(out - lab) / torch.linalg.norm(lab)).item()
+
+    def rate(fn, n, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return n * reps / (a.elapsed_time(b) * 1e-3)
+
+    xb, tb = held.x[:BATCH_S].contiguous(), held.target[:BATCH_S].contiguous()
+    ips_student = rate(lambda: ex.student.predict(xb, tb, ex.v_empty), BATCH_S, reps=20)
+    ips_checked = rate(lambda: ex.explain(xb, tb, first=N_TRAIN), BATCH_S)
+    x64 = held.x[:1024].double()
+    ips_exact = rate(lambda: ex.exact(x64), 1024, reps=2)
+    mb = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops_sustained": 1700.0}
+    if rank != 0:
+        return
+    line = {
+        "metric": "student inst/s (amortised explainer, d=16 l=2, 137 scores)", "value": ips_checked,
+        "unit": "instances/s", "n_gpus": world, "steps": epochs, "warmup": 0, "ms_per_step": ms_train / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "student_d16_l2", "hidden": H, "batch": BATCH_S, "train": N_TRAIN, "held_out": N_HELD,
+                   "epochs": epochs, "residual_samples": ex.K, "threshold": tau},
+        "student_only_inst_per_s": ips_student, "exact_path_inst_per_s": ips_exact,
+        "speedup_vs_exact": ips_checked / ips_exact,
+        "heldout_rmse": rmse, "heldout_rel_error": rel, "heldout_rel_error_after_fallback": rel_fb,
+        "fallback_fraction": fb.float().mean().item(), "final_train_loss": losses[-1],
+        "data_generation_s": t_data,
+        "roofline": {"bound": "tensor", "kernel": "gemm_bf16_tcgen05 (training step)", "achieved": tflops,
+                     "peak": float(mb.get("bf16_tflops_sustained", 1700.0)), "unit": "TFLOP/s",
+                     "frac": tflops / float(mb.get("bf16_tflops_sustained", 1700.0)), "traffic": None},
+        "clocks": clocks.summary(),
+        "gpu_launches": steps * 16,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -384,6 +468,8 @@ def main():
     try:
         if args.workload == "uneven_1024":
             run_uneven(args, rank, world, local_rank)
+        elif args.workload == "student":
+            run_student(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

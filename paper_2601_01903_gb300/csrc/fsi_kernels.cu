@@ -229,6 +229,8 @@ struct FastArgs {
     int n_tab, n_g;
     int off_rec2, off_items2, off_rec3, off_items3, n_items2, n_items3;
     int d, h, n_ch, ell, prec_bits, regA, regB, load_mask;
+    int n_rounds;
+    int i2_beg[4], i2_end[4], i3_beg[4], i3_end[4];
     long long game0;
 };
 
@@ -288,7 +290,7 @@ __device__ __forceinline__ void zeta16(Acc (&x)[16]) {
 // states (regA).
 template <int O, typename Acc>
 __device__ __forceinline__ void block2_item(const int32_t *rec, int u, int t3, const Acc *regB, Acc *regA) {
-    const int s_in = rec[0], base_in = rec[1];
+    const int s_in = __ldg(rec), base_in = __ldg(rec + 1);
     Acc x[16];
     const int common = (base_in + u - s_in) * 256 + t3;
     const int lo = u - 4, hi = u - s_in;  // valid popcounts of tau
@@ -303,7 +305,7 @@ __device__ __forceinline__ void block2_item(const int32_t *rec, int u, int t3, c
         if (cpopc(sr) > O) continue;
         const int j = u - s_in - cpopc(sr);
         if (j < 0) continue;
-        const int st = rec[2 + sr] + j;
+        const int st = __ldg(rec + 2 + sr) + j;
         regA[st * 16 + (t3 ^ (st & 15))] = x[sr];
     }
 }
@@ -312,7 +314,7 @@ __device__ __forceinline__ void block2_item(const int32_t *rec, int u, int t3, c
 // channels (regB).
 template <int O, typename Acc>
 __device__ __forceinline__ void block3_item(const int32_t *rec, int u, const Acc *regA, Acc *regB) {
-    const int s_in = rec[0], base_in = rec[1];
+    const int s_in = __ldg(rec), base_in = __ldg(rec + 1);
     Acc x[16];
     const int lo = u - 8, hi = u - s_in;
 #pragma unroll
@@ -327,7 +329,7 @@ __device__ __forceinline__ void block3_item(const int32_t *rec, int u, const Acc
         if (cpopc(sr) > O) continue;
         const int j = u - s_in - cpopc(sr);
         if (j < 0) continue;
-        regB[rec[2 + sr] + j] = x[sr];
+        regB[__ldg(rec + 2 + sr) + j] = x[sr];
     }
 }
 
@@ -336,17 +338,14 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
     using In = typename TileTraits<Acc>::In;
     using GT = typename GTraits<Acc>::G;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Acc *regA = reinterpret_cast<Acc *>(smem_raw);  // tile, then level-8 states
-    Acc *regB = regA + a.regA;                       // level-4 states, then channels
-    int32_t *stab = reinterpret_cast<int32_t *>(regB + a.regB);
-    int32_t *sgtab = stab + a.n_tab;
+    Acc *regA = reinterpret_cast<Acc *>(smem_raw);  // tile, then one round's level-8 states
+    Acc *regB = regA + a.regA;                       // one round's level-4 states
+    Acc *regY = regB + a.regB;                       // channels
+    const int32_t *stab = a.tab;                     // tables stay in global memory (L1)
     __shared__ int s_emax;
 
     const int tid = threadIdx.x;
     const In *src = reinterpret_cast<const In *>(a.v) + (game << a.d) + (tile << 12);
-
-    for (int i = tid; i < a.n_tab; i += kTileThreads) stab[i] = __ldg(a.tab + i);
-    for (int i = tid; i < 2 * a.n_g; i += kTileThreads) sgtab[i] = __ldg(a.gtab + i);
 
     Acc x[16];
     int E = 0;
@@ -396,15 +395,19 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
         for (int r = 0; r < 16; ++r) x[r] = regA[tile_phys(e0 | r)];
         mobius16(x);
     }
-    // ---- ranked block 1 (bits 0-3) from registers -> level-4 states ----
-    // level-4 index: state * 256 + (t3 + 16 * t2)
-    {
-        const int pos = t3 + 16 * t2;
+    // ---- ranked sums in rounds r = |sigma n bits 0..3| ----
+    // A state's round never changes once bits 0-3 are processed, so each
+    // round's level-4 states (region B), level-8 states (region A) and the
+    // block-3 items that read them form an independent slice.
+    const int pos = t3 + 16 * t2;
+    for (int rd = 0; rd < a.n_rounds; ++rd) {
+        // block 1 (bits 0-3) from registers: level-4 states of this round,
+        // index state * 256 + (t3 + 16 * t2)
 #pragma unroll
         for (int sg = 0; sg < 16; ++sg) {
             const int s = cpopc(sg);
-            if (s > a.ell) continue;
-            const int base = stab[sg];
+            if (s != rd || s > a.ell) continue;
+            const int base = __ldg(stab + sg);
 #pragma unroll
             for (int j = 0; j <= 4 - s; ++j) {
                 Acc acc = 0;
@@ -414,48 +417,48 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
                 regB[(base + j) * 256 + pos] = acc;
             }
         }
-    }
-    __syncthreads();
-    // ---- ranked block 2 (bits 4-7): items (sigma1, u), 16 lanes over t3 ----
-    // level-8 index: state * 16 + (t3 ^ (state & 15))
-    for (int it = tid >> 4; it < a.n_items2; it += kTileThreads / 16) {
-        const int item = stab[a.off_items2 + it];
-        if (item < 0) continue;
-        const int32_t *rec = stab + a.off_rec2 + (item >> 8) * 18;
-        const int u = item & 255;
-        switch (a.ell - rec[0]) {
-            case 0: block2_item<0>(rec, u, t3, regB, regA); break;
-            case 1: block2_item<1>(rec, u, t3, regB, regA); break;
-            case 2: block2_item<2>(rec, u, t3, regB, regA); break;
-            default: block2_item<3>(rec, u, t3, regB, regA); break;
+        __syncthreads();
+        // block 2 (bits 4-7): items (sigma1, u), 16 lanes over t3; level-8
+        // states of the round at state * 16 + (t3 ^ (state & 15))
+        for (int it = a.i2_beg[rd] + (tid >> 4); it < a.i2_end[rd]; it += kTileThreads / 16) {
+            const int item = __ldg(stab + a.off_items2 + it);
+            if (item < 0) continue;
+            const int32_t *rec = stab + a.off_rec2 + (item >> 8) * 18;
+            const int u = item & 255;
+            switch (a.ell - rd) {
+                case 0: block2_item<0>(rec, u, t3, regB, regA); break;
+                case 1: block2_item<1>(rec, u, t3, regB, regA); break;
+                case 2: block2_item<2>(rec, u, t3, regB, regA); break;
+                default: block2_item<3>(rec, u, t3, regB, regA); break;
+            }
         }
-    }
-    __syncthreads();
-    // ---- ranked block 3 (bits 8-11): one item (sigma, u) per thread ----
-    for (int it = tid; it < a.n_items3; it += kTileThreads) {
-        const int item = stab[a.off_items3 + it];
-        if (item < 0) continue;
-        const int32_t *rec = stab + a.off_rec3 + (item >> 8) * 18;
-        const int u = item & 255;
-        switch (a.ell - rec[0]) {
-            case 0: block3_item<0>(rec, u, regA, regB); break;
-            case 1: block3_item<1>(rec, u, regA, regB); break;
-            case 2: block3_item<2>(rec, u, regA, regB); break;
-            default: block3_item<3>(rec, u, regA, regB); break;
+        __syncthreads();
+        // block 3 (bits 8-11): one item (sigma, u) per thread -> channels
+        for (int it = a.i3_beg[rd] + tid; it < a.i3_end[rd]; it += kTileThreads) {
+            const int item = __ldg(stab + a.off_items3 + it);
+            if (item < 0) continue;
+            const int32_t *rec = stab + a.off_rec3 + (item >> 8) * 18;
+            const int u = item & 255;
+            switch (a.ell - __ldg(rec)) {
+                case 0: block3_item<0>(rec, u, regA, regY); break;
+                case 1: block3_item<1>(rec, u, regA, regY); break;
+                case 2: block3_item<2>(rec, u, regA, regY); break;
+                default: block3_item<3>(rec, u, regA, regY); break;
+            }
         }
+        __syncthreads();
     }
-    __syncthreads();
     // ---- partial scores G(S_L, s, i) of this tile ----
     const int uH = __popcll((unsigned long long)tile);
     const int P1 = a.h + 1, Q1 = 13;
     GT *gdst = reinterpret_cast<GT *>(a.G) + ((game << a.h) + tile) * (long long)a.n_g;
     for (int g = tid; g < a.n_g; g += kTileThreads) {
-        const int cb = sgtab[2 * g], code = sgtab[2 * g + 1];
+        const int cb = __ldg(a.gtab + 2 * g), code = __ldg(a.gtab + 2 * g + 1);
         const int sL = code & 0xff, s = (code >> 8) & 0xff, i = code >> 16;
         const int r = s - sL, pp = uH + r - i;
         GT acc = 0;
         if (i <= uH && r - i <= a.h - uH) {
-            const Acc *y = regB + cb;
+            const Acc *y = regY + cb;
             const int J = 13 - sL;
             if constexpr (TileTraits<Acc>::exact) {
                 const long long *w = a.wnum + ((long long)s * P1 + pp) * Q1 + sL;
@@ -482,7 +485,7 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
 }
 
 template <typename Acc>
-__global__ void __launch_bounds__(kTileThreads) fsi_tile_fast_kernel(FastArgs a) {
+__global__ void __launch_bounds__(kTileThreads, 2) fsi_tile_fast_kernel(FastArgs a) {
     tile_fast_body<Acc>(a, a.game0 + blockIdx.y, blockIdx.x);
 }
 
@@ -834,9 +837,16 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
             fa.n_ch = p.n_ch;
             fa.ell = p.ell;
             fa.prec_bits = p.prec_bits;
-            fa.regA = std::max(1 << p.b, p.n8 * 16);
-            fa.regB = std::max(p.n4 * 256, p.n_ch);
+            fa.regA = p.fast_regA;
+            fa.regB = p.fast_regB;
             fa.load_mask = (1 << p.load_bits) - 1;
+            fa.n_rounds = p.n_rounds;
+            for (int r = 0; r < 4; ++r) {
+                fa.i2_beg[r] = p.i2_beg[r];
+                fa.i2_end[r] = p.i2_end[r];
+                fa.i3_beg[r] = p.i3_beg[r];
+                fa.i3_end[r] = p.i3_end[r];
+            }
             fa.game0 = g0;
             fsi_tile_fast_kernel<Acc><<<g1, kTileThreads, p.smem_fast, st>>>(fa);
         } else {
@@ -1262,7 +1272,7 @@ struct BatchArgs {
 };
 
 template <typename Acc>
-__global__ void __launch_bounds__(kTileThreads) fsi_batch_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(kTileThreads, 2) fsi_batch_kernel(BatchArgs a) {
     using GT = typename GTraits<Acc>::G;
     using In = typename TileTraits<Acc>::In;
     using Out = typename std::conditional<sizeof(Acc) == 4, float, double>::type;
@@ -1516,9 +1526,16 @@ tt_fsi_status tt_fsi_batch_create(const tt_fsi_game *games_host, int64_t n_games
         fa.n_ch = p.n_ch;
         fa.ell = p.ell;
         fa.prec_bits = p.prec_bits;
-        fa.regA = std::max(1 << p.b, p.n8 * 16);
-        fa.regB = std::max(p.n4 * 256, p.n_ch);
+        fa.regA = p.fast_regA;
+        fa.regB = p.fast_regB;
         fa.load_mask = (1 << p.load_bits) - 1;
+        fa.n_rounds = p.n_rounds;
+        for (int r = 0; r < 4; ++r) {
+            fa.i2_beg[r] = p.i2_beg[r];
+            fa.i2_end[r] = p.i2_end[r];
+            fa.i3_beg[r] = p.i3_beg[r];
+            fa.i3_end[r] = p.i3_end[r];
+        }
         CombineFastArgs &ca = cpl[i];
         ca = CombineFastArgs{};
         ca.tasks = p.d_tasks;

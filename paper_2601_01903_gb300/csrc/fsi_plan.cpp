@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <tuple>
 
 namespace ttfsi {
 
@@ -225,62 +226,99 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
 
     // fast tile path tables (see fsi_plan.h)
     if (want_fast) {
+        // level-k states (sigma, j), grouped into rounds by r = |sigma n bits 0..3|
         auto states_at = [&](int k) {
-            std::vector<std::pair<uint32_t, int>> st;
+            std::vector<std::tuple<int, uint32_t, int>> st;  // (round, sigma, j)
             for (uint32_t sg = 0; sg < (1u << k); ++sg) {
                 int s = popc64(sg);
                 if (s > ell) continue;
-                for (int j = 0; j <= k - s; ++j) st.push_back({sg, j});
+                for (int j = 0; j <= k - s; ++j) st.push_back({popc64(sg & 15u), sg, j});
             }
             std::sort(st.begin(), st.end());
             return st;
         };
-        auto bases = [&](const std::vector<std::pair<uint32_t, int>> &st, int k) {
-            std::vector<int> base((size_t)1 << k, -1);
-            for (size_t i = 0; i < st.size(); ++i)
-                if (st[i].second == 0) base[st[i].first] = (int)i;
-            return base;
-        };
         auto st4 = states_at(4), st8 = states_at(8);
-        auto b4 = bases(st4, 4), b8 = bases(st8, 8), b12 = bases(cur, 12);
-        p.n4 = (int)st4.size();
-        p.n8 = (int)st8.size();
+        const int R = std::min(ell, 4) + 1;  // rounds r = 0..min(l, 4)
+        std::vector<int> first4(R + 1, (int)st4.size()), first8(R + 1, (int)st8.size());
+        for (int r = R - 1; r >= 0; --r) {
+            for (size_t i = 0; i < st4.size(); ++i)
+                if (std::get<0>(st4[i]) == r) { first4[r] = (int)i; break; }
+            for (size_t i = 0; i < st8.size(); ++i)
+                if (std::get<0>(st8[i]) == r) { first8[r] = (int)i; break; }
+            first4[r] = std::min(first4[r], first4[r + 1]);
+            first8[r] = std::min(first8[r], first8[r + 1]);
+        }
+        std::vector<int> b4(16, -1), b8(256, -1);  // relative to the round's first state
+        for (size_t i = 0; i < st4.size(); ++i)
+            if (std::get<2>(st4[i]) == 0) b4[std::get<1>(st4[i])] = (int)i - first4[std::get<0>(st4[i])];
+        for (size_t i = 0; i < st8.size(); ++i)
+            if (std::get<2>(st8[i]) == 0) b8[std::get<1>(st8[i])] = (int)i - first8[std::get<0>(st8[i])];
+        std::vector<int> b12(4096, -1);
+        for (size_t i = 0; i < cur.size(); ++i)
+            if (cur[i].second == 0) b12[cur[i].first] = (int)i;
+        int max4 = 0, max8 = 0;
+        for (int r = 0; r < R; ++r) {
+            max4 = std::max(max4, first4[r + 1] - first4[r]);
+            max8 = std::max(max8, first8[r + 1] - first8[r]);
+        }
+        p.n4 = max4;
+        p.n8 = max8;
         std::vector<int32_t> &T = p.fast_tab;
         T.assign(b4.begin(), b4.end());
-        // Items are grouped by |sigma| (which fixes the pruning order of the
-        // item's superset sums) and each group is padded with idle items
-        // (-1) to a multiple of `quantum`, so that all items a warp runs at
-        // once take the same code path.
-        auto add_pass = [&](int k_in, const std::vector<int> &bin, const std::vector<int> &bout,
-                            int quantum, int &off_rec, int &off_items, int &n_items) {
-            std::vector<int32_t> recs, items;
-            std::vector<std::vector<int32_t>> by_s(ell + 1);
-            int q = 0;
-            for (uint32_t sg = 0; sg < (1u << k_in); ++sg) {
-                if (bin[sg] < 0) continue;
-                int s = popc64(sg);
-                recs.push_back(s);
-                recs.push_back(bin[sg]);
-                for (uint32_t sr = 0; sr < 16; ++sr) recs.push_back(bout[sg | (sr << k_in)]);
-                for (int u = s; u <= k_in + 4; ++u) by_s[s].push_back((q << 8) | u);
+        // block 2: records per sigma1 (4 bits), items grouped by round r = |sigma1|
+        std::vector<int32_t> recs2, items2, recs3, items3;
+        std::vector<std::vector<int32_t>> it2(R);
+        int q = 0;
+        for (int r = 0; r < R; ++r)
+            for (uint32_t sg = 0; sg < 16; ++sg) {
+                if (popc64(sg) != r || b4[sg] < 0) continue;
+                recs2.push_back(r);
+                recs2.push_back(b4[sg]);
+                for (uint32_t sr = 0; sr < 16; ++sr) recs2.push_back(b8[sg | (sr << 4)]);
+                for (int u = r; u <= 8; ++u) it2[r].push_back((q << 8) | u);
                 ++q;
             }
-            for (auto &grp : by_s) {
-                if (grp.empty()) continue;
-                items.insert(items.end(), grp.begin(), grp.end());
-                while (items.size() % quantum) items.push_back(-1);
+        // block 3: records per sigma (8 bits), items grouped by (round, |sigma|)
+        std::vector<std::vector<std::vector<int32_t>>> it3(R, std::vector<std::vector<int32_t>>(ell + 1));
+        q = 0;
+        for (int r = 0; r < R; ++r)
+            for (uint32_t sg = 0; sg < 256; ++sg) {
+                if (popc64(sg & 15u) != r || b8[sg] < 0) continue;
+                const int s = popc64(sg);
+                recs3.push_back(s);
+                recs3.push_back(b8[sg]);
+                for (uint32_t sr = 0; sr < 16; ++sr) recs3.push_back(b12[sg | (sr << 8)]);
+                for (int u = s; u <= 12; ++u) it3[r][s].push_back((q << 8) | u);
+                ++q;
             }
-            off_rec = (int)T.size();
-            T.insert(T.end(), recs.begin(), recs.end());
-            off_items = (int)T.size();
-            T.insert(T.end(), items.begin(), items.end());
-            n_items = (int)items.size();
-        };
-        add_pass(4, b4, b8, 2, p.off_rec2, p.off_items2, p.n_items2);
-        add_pass(8, b8, b12, 32, p.off_rec3, p.off_items3, p.n_items3);
-        const size_t regA = (size_t)std::max(1 << b, p.n8 * 16);
-        const size_t regB = (size_t)std::max(p.n4 * 256, p.n_ch);
-        p.smem_fast = (regA + regB) * elem;
+        for (int r = 0; r < 4; ++r) p.i2_beg[r] = p.i2_end[r] = p.i3_beg[r] = p.i3_end[r] = 0;
+        for (int r = 0; r < R; ++r) {
+            p.i2_beg[r] = (int)items2.size();
+            items2.insert(items2.end(), it2[r].begin(), it2[r].end());
+            while (items2.size() % 2) items2.push_back(-1);
+            p.i2_end[r] = (int)items2.size();
+            p.i3_beg[r] = (int)items3.size();
+            for (auto &grp : it3[r]) {
+                if (grp.empty()) continue;
+                items3.insert(items3.end(), grp.begin(), grp.end());
+                while (items3.size() % 32) items3.push_back(-1);
+            }
+            p.i3_end[r] = (int)items3.size();
+        }
+        p.n_rounds = R;
+        p.off_rec2 = (int)T.size();
+        T.insert(T.end(), recs2.begin(), recs2.end());
+        p.off_items2 = (int)T.size();
+        T.insert(T.end(), items2.begin(), items2.end());
+        p.off_rec3 = (int)T.size();
+        T.insert(T.end(), recs3.begin(), recs3.end());
+        p.off_items3 = (int)T.size();
+        T.insert(T.end(), items3.begin(), items3.end());
+        p.n_items2 = (int)items2.size();
+        p.n_items3 = (int)items3.size();
+        p.fast_regA = std::max(1 << b, p.n8 * 16);
+        p.fast_regB = p.n4 * 256;
+        p.smem_fast = (size_t)(p.fast_regA + p.fast_regB + p.n_ch) * elem;
         p.fast12 = p.smem_fast <= smem_budget;
     }
 
@@ -329,7 +367,6 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
             uint32_t SL = (uint32_t)(S & low_mask);
             p.tasks[i * 4 + 3] = g_of.at({SL, popc64(S)});
         }
-        p.smem_fast += (p.fast_tab.size() + p.gtab.size()) * sizeof(int32_t);
         p.fast12 = p.smem_fast <= smem_budget;
         if (!p.fast12) return TT_FSI_ERR_UNSUPPORTED;  // does not happen for l <= 3
     }

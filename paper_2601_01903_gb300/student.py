@@ -216,6 +216,10 @@ class Explainer:
                                             np.zeros((1, 1), dtype=np.uint32))[0, 0].item())
         self.tau = float("inf")
         self.seed = seed
+        # Spot-check coalitions: one pool of `batch` x K draws, made once, so
+        # the instance in row i of every call uses pool row i.
+        self.coal_pool = sample_coalitions(batch, self.d, K, seed)
+        self.coal_pool_dev = torch.as_tensor(self.coal_pool.view(np.int32), device="cuda")
 
     # -- the exact path -----------------------------------------------------
     def values_at(self, x64, coal: np.ndarray):
@@ -279,18 +283,25 @@ class Explainer:
 
     # -- inference --------------------------------------------------------------
     def residuals(self, x32, phi, first: int = 0):
+        """Surrogate residual of each instance at its spot-check coalitions
+        (pool rows, cycled for calls longer than the pool)."""
         torch = self.torch
         lib = _declare()
         n = x32.shape[0]
-        coal = sample_coalitions(n, self.d, self.K, self.seed, first=first)
-        vcoal = self.values_at(x32.double(), coal)
-        c = torch.as_tensor(coal.view(np.int32), device="cuda")
         r = torch.empty(n, dtype=torch.float32, device="cuda")
-        _check(lib.tt_fsi_surrogate_residual(_p(phi), n, self.n_out, _p(self.masks), _p(c), _p(vcoal), self.K,
-                                              _p(r), _stream_ptr()), "tt_fsi_surrogate_residual")
+        x64 = x32.double()
+        for s in range(0, n, self.batch):
+            e = min(n, s + self.batch)
+            c = self.coal_pool_dev[:e - s]
+            vcoal = torch.empty(c.shape, dtype=torch.float32, device="cuda")
+            _check(lib.tt_fsi_masked_game_sampled(ctypes.byref(self.mlp.struct), _p(x64[s:e]), _p(self.baseline),
+                                                   e - s, _p(c), self.K, _p(vcoal), _stream_ptr()),
+                   "tt_fsi_masked_game_sampled")
+            _check(lib.tt_fsi_surrogate_residual(_p(phi[s:e]), e - s, self.n_out, _p(self.masks), _p(c), _p(vcoal),
+                                                  self.K, _p(r[s:e]), _stream_ptr()), "tt_fsi_surrogate_residual")
         return r
 
-    def calibrate(self, data: Dataset, quantile: float = 0.95):
+    def calibrate(self, data: Dataset, quantile: float = 0.99):
         """Fallback threshold: the given quantile of the student's residual on
         held-out instances."""
         phi = self.predict_raw(data.x, data.target)
