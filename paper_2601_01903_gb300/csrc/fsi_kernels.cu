@@ -24,6 +24,7 @@
 #include <new>
 #include <vector>
 
+#include "fast_layout.h"
 #include "fsi_plan.h"
 #include "tt_fsi.h"
 
@@ -198,15 +199,21 @@ __global__ void __launch_bounds__(kTileThreads) fsi_tile_kernel(TileArgs a) {
 // every half-warp on 16 distinct 8-byte bank pairs in all three phases.
 //
 // Ranked superset sums (the (|S|, |T|) counters of Section 3.3) in three
-// 4-bit blocks.  A state after k bits is (sigma, j): sigma = the output's
-// part on the processed bits (|sigma| <= l), j = |T \ S| on those bits.
-// Block 1 runs on the registers left by the last Moebius phase.  Blocks 2
-// and 3 run items (sigma, u) where u = |T| minus the popcount of the
-// untouched high bits: an item gathers its 16 inputs (one rank each,
-// j = u - |sigma| - |tau|), forms the plain superset sums over the 4 new bits
-// in registers (only those with |sigma u sigma_r| <= l) and writes each
-// (sigma u sigma_r, u - |sigma u sigma_r|) once, so no two threads ever
-// write the same state.
+// 4-bit groups, ranked by the absolute count u = |T n processed bits| (the
+// layout and its closed-form offsets are in fast_layout.h).  With u fixed,
+// every input of a group step has exactly one rank, so each step is a plain
+// superset sum over 4 bits in registers:
+//   block 1 (group A, registers): Z_A(sigma_A, t) from the Moebius values;
+//   block 2 (group B): item (sigma_A, u) x 16 lanes tau_C gathers the 16
+//     values Z_A(sigma_A, u - |tau_B|; tau_B) and writes Z_AB(sigma_A u
+//     sigma_B, u) for every sigma_B the order allows;
+//   block 3 (group C): item (sigma_8, u') per thread gathers Z_AB(sigma_8,
+//     u' - |tau_C|; tau_C) and writes the channels Z(sigma_8 u sigma_C, u').
+// Each output state is written by exactly one thread.  States are processed
+// in rounds rd = |sigma_A| (a state's round never changes), so only one
+// round's level-4 and level-8 states are held in shared memory at a time.
+// The kernel is instantiated per order l, which makes every offset and
+// every pruning decision a compile-time constant.
 //
 // Weighting: the tile, whose high pattern U_H has u_H = |U_H| set bits, forms
 // one partial score per (S_L, s, i) -- i the size of U_H n S_H that a score
@@ -220,17 +227,13 @@ struct FastArgs {
     void *G;
     int *tile_exp;
     int *err;
-    const int32_t *tab;
     const int32_t *gtab;
     const long long *wnum;
     const long long *wden;
     const double *wf64;
     const float *wf32;
-    int n_tab, n_g;
-    int off_rec2, off_items2, off_rec3, off_items3, n_items2, n_items3;
-    int d, h, n_ch, ell, prec_bits, regA, regB, load_mask;
-    int n_rounds;
-    int i2_beg[4], i2_end[4], i3_beg[4], i3_end[4];
+    int n_g;
+    int d, h, ell, prec_bits, load_mask;
     long long game0;
 };
 
@@ -260,10 +263,6 @@ __device__ __forceinline__ __int128 mul_wide(long long a, long long b) {
 
 __device__ __forceinline__ int tile_phys(int e) { return e ^ ((e >> 8) & 15); }
 
-// Popcount of a 4-bit value, written out so that it folds to a constant in
-// unrolled loops.
-__host__ __device__ constexpr int cpopc(int x) { return (x & 1) + ((x >> 1) & 1) + ((x >> 2) & 1) + ((x >> 3) & 1); }
-
 template <typename Acc>
 __device__ __forceinline__ void mobius16(Acc (&x)[16]) {
 #pragma unroll
@@ -283,65 +282,151 @@ __device__ __forceinline__ void zeta16(Acc (&x)[16]) {
     for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int r = 0; r < 16; ++r)
-            if (!((r >> q) & 1) && cpopc(r & ((1 << q) - 1)) <= O) x[r] += x[r | (1 << q)];
+            if (!((r >> q) & 1) && fast::pc4(r & ((1 << q) - 1)) <= O) x[r] += x[r | (1 << q)];
 }
 
-// Block 2 item: inputs from the level-4 states (regB), outputs to the level-8
-// states (regA).
-template <int O, typename Acc>
-__device__ __forceinline__ void block2_item(const int32_t *rec, int u, int t3, const Acc *regB, Acc *regA) {
-    const int s_in = __ldg(rec), base_in = __ldg(rec + 1);
+// Block 1 of round RD: the level-4 states (sigma_A, t), |sigma_A| = RD, of
+// this thread's position (tau_B, tau_C) from its 16 Moebius values.
+template <int L, int RD, typename Acc>
+__device__ __forceinline__ void fast_block1(const Acc (&x)[16], Acc *regB, int pos) {
+#pragma unroll
+    for (int sg = 0; sg < 16; ++sg) {
+        if (fast::pc4(sg) != RD) continue;
+        const int base = fast::rank4(sg) * (5 - RD) - RD;
+#pragma unroll
+        for (int t = RD; t <= 4; ++t) {
+            Acc acc = 0;
+#pragma unroll
+            for (int tau = 0; tau < 16; ++tau)
+                if ((tau & sg) == sg && fast::pc4(tau) == t) acc += x[tau];
+            regB[(base + t) * 256 + pos] = acc;
+        }
+    }
+}
+
+// Block 2 of round RD: items (rank sigma_A, u), u in [RD, 8], 16 lanes over
+// tau_C.  Level-8 states go to regA[tau_C * NST + state].
+template <int L, int RD, typename Acc>
+__device__ __forceinline__ void fast_block2(const Acc *regB, Acc *regA, int tid) {
+    constexpr int O = L - RD;
+    constexpr int NU = 9 - RD;
+    constexpr int NIT = fast::c4(RD) * NU;
+    constexpr int S8 = fast::s8(L, RD);
+    constexpr int NST = fast::nst(L);
+    const int t3 = tid & 15;
+    for (int it = tid >> 4; it < NIT; it += kTileThreads / 16) {
+        const int rA = it / NU, uu = it - rA * NU;  // u = RD + uu
+        // input tau_B: level-4 state (sigma_A, t = u - |tau_B|), t in [RD, 4]
+        const Acc *src = regB + (rA * (5 - RD) + uu) * 256 + t3;
+        Acc x[16];
+#pragma unroll
+        for (int tau = 0; tau < 16; ++tau) {
+            const int pc = fast::pc4(tau);
+            Acc val = 0;
+            if (uu >= pc && uu - pc <= 4 - RD) val = src[16 * tau - 256 * pc];
+            x[tau] = val;
+        }
+        zeta16<O>(x);
+        Acc *dst = regA + t3 * NST + rA * S8 + uu;
+#pragma unroll
+        for (int sb = 0; sb < 16; ++sb) {
+            const int kB = fast::pc4(sb);
+            if (kB > O) continue;
+            // state (sigma_A u sigma_B, u): off8 + rank * (9 - RD - kB) + (u - RD - kB)
+            if (uu >= kB) dst[fast::off8(RD, kB) + fast::rank4(sb) * (9 - RD - kB) - kB] = x[sb];
+        }
+    }
+}
+
+// Block 3 item of round RD, group kB = |sigma_B|: (rank sigma_A, rank
+// sigma_B, u'), u' in [RD + KB, 12]; writes the channels of sigma_8 u sigma_C.
+template <int L, int RD, int KB, typename Acc>
+__device__ __forceinline__ void fast_block3_item(int local, const Acc *regA, Acc *regY) {
+    constexpr int K8 = RD + KB;
+    constexpr int O = L - K8;
+    constexpr int NU = 13 - K8;
+    constexpr int NB = fast::c4(KB);
+    constexpr int S8 = fast::s8(L, RD);
+    constexpr int NST = fast::nst(L);
+    constexpr int OFF8 = fast::off8(RD, KB);
+    constexpr int CG = fast::chan_group(L, RD, KB);
+    constexpr int CH = fast::ch8(L, K8);
+    const int pair = local / NU, uu = local - pair * NU;  // u' = K8 + uu
+    const int rA = pair / NB, rB = pair - rA * NB;
+    // input tau_C: level-8 state (sigma_8, u' - |tau_C|), u' - |tau_C| in [K8, 8]
+    const Acc *src = regA + rA * S8 + OFF8 + rB * (9 - K8) + uu;
     Acc x[16];
-    const int common = (base_in + u - s_in) * 256 + t3;
-    const int lo = u - 4, hi = u - s_in;  // valid popcounts of tau
 #pragma unroll
     for (int tau = 0; tau < 16; ++tau) {
-        const int pc = cpopc(tau);
-        x[tau] = (pc >= lo && pc <= hi) ? regB[common + 16 * tau - 256 * pc] : (Acc)0;
+        const int pc = fast::pc4(tau);
+        Acc val = 0;
+        if (uu >= pc && uu - pc <= 8 - K8) val = src[tau * NST - pc];
+        x[tau] = val;
     }
     zeta16<O>(x);
+    Acc *dst = regY + CG + pair * CH + uu;
 #pragma unroll
-    for (int sr = 0; sr < 16; ++sr) {
-        if (cpopc(sr) > O) continue;
-        const int j = u - s_in - cpopc(sr);
-        if (j < 0) continue;
-        const int st = __ldg(rec + 2 + sr) + j;
-        regA[st * 16 + (t3 ^ (st & 15))] = x[sr];
+    for (int sc = 0; sc < 16; ++sc) {
+        const int kC = fast::pc4(sc);
+        if (kC > O) continue;
+        // channel (sigma_8 u sigma_C, j = u' - K8 - kC)
+        if (uu >= kC) dst[fast::offC(K8, kC) + fast::rank4(sc) * (13 - K8 - kC) - kC] = x[sc];
     }
 }
 
-// Block 3 item: inputs from the level-8 states (regA), outputs to the
-// channels (regB).
-template <int O, typename Acc>
-__device__ __forceinline__ void block3_item(const int32_t *rec, int u, const Acc *regA, Acc *regB) {
-    const int s_in = __ldg(rec), base_in = __ldg(rec + 1);
-    Acc x[16];
-    const int lo = u - 8, hi = u - s_in;
-#pragma unroll
-    for (int tau = 0; tau < 16; ++tau) {
-        const int pc = cpopc(tau);
-        const int st = base_in + u - s_in - pc;
-        x[tau] = (pc >= lo && pc <= hi) ? regA[st * 16 + (tau ^ (st & 15))] : (Acc)0;
-    }
-    zeta16<O>(x);
-#pragma unroll
-    for (int sr = 0; sr < 16; ++sr) {
-        if (cpopc(sr) > O) continue;
-        const int j = u - s_in - cpopc(sr);
-        if (j < 0) continue;
-        regB[__ldg(rec + 2 + sr) + j] = x[sr];
+// Block 3 of round RD: the groups kB = 0..L-RD one after another, each
+// padded to whole warps so that a warp never mixes two pruning orders.
+template <int L, int RD, typename Acc>
+__device__ __forceinline__ void fast_block3(const Acc *regA, Acc *regY, int tid) {
+    constexpr int M = L - RD;
+    constexpr int P0 = fast::pad32(fast::g3(RD, 0));
+    constexpr int P1 = M >= 1 ? fast::pad32(fast::g3(RD, 1)) : 0;
+    constexpr int P2 = M >= 2 ? fast::pad32(fast::g3(RD, 2)) : 0;
+    constexpr int P3 = M >= 3 ? fast::pad32(fast::g3(RD, 3)) : 0;
+    constexpr int TOTAL = P0 + P1 + P2 + P3;
+    for (int it = tid; it < TOTAL; it += kTileThreads) {
+        if (it < P0) {
+            if (it < fast::g3(RD, 0)) fast_block3_item<L, RD, 0>(it, regA, regY);
+        } else if (it < P0 + P1) {
+            if constexpr (M >= 1) {
+                const int l = it - P0;
+                if (l < fast::g3(RD, 1)) fast_block3_item<L, RD, 1>(l, regA, regY);
+            }
+        } else if (it < P0 + P1 + P2) {
+            if constexpr (M >= 2) {
+                const int l = it - P0 - P1;
+                if (l < fast::g3(RD, 2)) fast_block3_item<L, RD, 2>(l, regA, regY);
+            }
+        } else {
+            if constexpr (M >= 3) {
+                const int l = it - P0 - P1 - P2;
+                if (l < fast::g3(RD, 3)) fast_block3_item<L, RD, 3>(l, regA, regY);
+            }
+        }
     }
 }
 
-template <typename Acc>
+// Round RD: blocks 2 and 3, then block 1 of the next round, which only
+// touches the level-4 region that block 2 has finished reading.
+template <int L, int RD, typename Acc>
+__device__ __forceinline__ void fast_round(const Acc (&x)[16], Acc *regA, Acc *regB, Acc *regY, int tid,
+                                           int pos) {
+    fast_block2<L, RD>(regB, regA, tid);
+    __syncthreads();
+    fast_block3<L, RD>(regA, regY, tid);
+    if constexpr (RD < L) fast_block1<L, RD + 1>(x, regB, pos);
+    __syncthreads();
+    if constexpr (RD < L) fast_round<L, RD + 1>(x, regA, regB, regY, tid, pos);
+}
+
+template <typename Acc, int L>
 __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long long game, const long long tile) {
     using In = typename TileTraits<Acc>::In;
     using GT = typename GTraits<Acc>::G;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Acc *regA = reinterpret_cast<Acc *>(smem_raw);  // tile, then one round's level-8 states
-    Acc *regB = regA + a.regA;                       // one round's level-4 states
-    Acc *regY = regB + a.regB;                       // channels
-    const int32_t *stab = a.tab;                     // tables stay in global memory (L1)
+    Acc *regB = regA + fast::regA_elems(L);          // one round's level-4 states
+    Acc *regY = regB + fast::regB_elems(L);          // channels
     __shared__ int s_emax;
 
     const int tid = threadIdx.x;
@@ -387,7 +472,7 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
         for (int r = 0; r < 16; ++r) regA[tile_phys(e0 | (r << 4))] = x[r];
     }
     __syncthreads();
-    // ---- bits 0-3: t3 = tid & 15 (bits 8-11), t2 = tid >> 4 (bits 4-7) ----
+    // ---- bits 0-3: t3 = tid & 15 (tau_C, bits 8-11), t2 = tid >> 4 (tau_B, bits 4-7) ----
     const int t3 = tid & 15, t2 = tid >> 4;
     {
         const int e0 = (t2 << 4) | (t3 << 8);
@@ -395,59 +480,11 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
         for (int r = 0; r < 16; ++r) x[r] = regA[tile_phys(e0 | r)];
         mobius16(x);
     }
-    // ---- ranked sums in rounds r = |sigma n bits 0..3| ----
-    // A state's round never changes once bits 0-3 are processed, so each
-    // round's level-4 states (region B), level-8 states (region A) and the
-    // block-3 items that read them form an independent slice.
+    // ---- ranked sums: block 1 of round 0, then the rounds ----
     const int pos = t3 + 16 * t2;
-    for (int rd = 0; rd < a.n_rounds; ++rd) {
-        // block 1 (bits 0-3) from registers: level-4 states of this round,
-        // index state * 256 + (t3 + 16 * t2)
-#pragma unroll
-        for (int sg = 0; sg < 16; ++sg) {
-            const int s = cpopc(sg);
-            if (s != rd || s > a.ell) continue;
-            const int base = __ldg(stab + sg);
-#pragma unroll
-            for (int j = 0; j <= 4 - s; ++j) {
-                Acc acc = 0;
-#pragma unroll
-                for (int tau = 0; tau < 16; ++tau)
-                    if ((tau & sg) == sg && cpopc(tau & ~sg) == j) acc += x[tau];
-                regB[(base + j) * 256 + pos] = acc;
-            }
-        }
-        __syncthreads();
-        // block 2 (bits 4-7): items (sigma1, u), 16 lanes over t3; level-8
-        // states of the round at state * 16 + (t3 ^ (state & 15))
-        for (int it = a.i2_beg[rd] + (tid >> 4); it < a.i2_end[rd]; it += kTileThreads / 16) {
-            const int item = __ldg(stab + a.off_items2 + it);
-            if (item < 0) continue;
-            const int32_t *rec = stab + a.off_rec2 + (item >> 8) * 18;
-            const int u = item & 255;
-            switch (a.ell - rd) {
-                case 0: block2_item<0>(rec, u, t3, regB, regA); break;
-                case 1: block2_item<1>(rec, u, t3, regB, regA); break;
-                case 2: block2_item<2>(rec, u, t3, regB, regA); break;
-                default: block2_item<3>(rec, u, t3, regB, regA); break;
-            }
-        }
-        __syncthreads();
-        // block 3 (bits 8-11): one item (sigma, u) per thread -> channels
-        for (int it = a.i3_beg[rd] + tid; it < a.i3_end[rd]; it += kTileThreads) {
-            const int item = __ldg(stab + a.off_items3 + it);
-            if (item < 0) continue;
-            const int32_t *rec = stab + a.off_rec3 + (item >> 8) * 18;
-            const int u = item & 255;
-            switch (a.ell - __ldg(rec)) {
-                case 0: block3_item<0>(rec, u, regA, regY); break;
-                case 1: block3_item<1>(rec, u, regA, regY); break;
-                case 2: block3_item<2>(rec, u, regA, regY); break;
-                default: block3_item<3>(rec, u, regA, regY); break;
-            }
-        }
-        __syncthreads();
-    }
+    fast_block1<L, 0>(x, regB, pos);
+    __syncthreads();
+    fast_round<L, 0>(x, regA, regB, regY, tid, pos);
     // ---- partial scores G(S_L, s, i) of this tile ----
     const int uH = __popcll((unsigned long long)tile);
     const int P1 = a.h + 1, Q1 = 13;
@@ -484,9 +521,19 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
     }
 }
 
+// One tile of a plan with order a.ell (1..3): the instantiation for that order.
 template <typename Acc>
+__device__ __forceinline__ void tile_fast_dispatch(const FastArgs &a, const long long game, const long long tile) {
+    switch (a.ell) {
+        case 1: tile_fast_body<Acc, 1>(a, game, tile); break;
+        case 2: tile_fast_body<Acc, 2>(a, game, tile); break;
+        default: tile_fast_body<Acc, 3>(a, game, tile); break;
+    }
+}
+
+template <typename Acc, int L>
 __global__ void __launch_bounds__(kTileThreads, 2) fsi_tile_fast_kernel(FastArgs a) {
-    tile_fast_body<Acc>(a, a.game0 + blockIdx.y, blockIdx.x);
+    tile_fast_body<Acc, L>(a, a.game0 + blockIdx.y, blockIdx.x);
 }
 
 // ----------------------------------------------------------------------------
@@ -721,7 +768,7 @@ struct TableRef {
     size_t bytes;
 };
 
-constexpr int kPlanTables = 8;
+constexpr int kPlanTables = 7;
 
 std::array<TableRef, kPlanTables> plan_tables(Plan &p) {
     return {{
@@ -731,7 +778,6 @@ std::array<TableRef, kPlanTables> plan_tables(Plan &p) {
         {(void **)&p.d_wden, p.wden.data(), p.wden.size() * sizeof(long long)},
         {(void **)&p.d_wf64, p.wf64.data(), p.wf64.size() * sizeof(double)},
         {(void **)&p.d_wf32, p.wf32.data(), p.wf32.size() * sizeof(float)},
-        {(void **)&p.d_fast_tab, p.fast_tab.data(), p.fast_tab.size() * sizeof(int32_t)},
         {(void **)&p.d_gtab, p.gtab.data(), p.gtab.size() * sizeof(int32_t)},
     }};
 }
@@ -758,8 +804,33 @@ void free_plan_device(Plan *p) {
     cudaFree(p->d_Y);
     cudaFree(p->d_exp);
     cudaFree(p->d_err);
-    cudaFree(p->d_fast_tab);
     cudaFree(p->d_gtab);
+}
+
+// Kernel arguments of a fast-path plan that do not depend on the call.
+FastArgs fast_args(const Plan &p) {
+    FastArgs fa{};
+    fa.gtab = p.d_gtab;
+    fa.wnum = p.d_wnum;
+    fa.wden = p.d_wden;
+    fa.wf64 = p.d_wf64;
+    fa.wf32 = p.d_wf32;
+    fa.n_g = p.n_g;
+    fa.d = p.d;
+    fa.h = p.h;
+    fa.ell = p.ell;
+    fa.prec_bits = p.prec_bits;
+    fa.load_mask = (1 << p.load_bits) - 1;
+    return fa;
+}
+
+// Raises the shared-memory cap of every order's fast tile kernel.
+template <typename Acc>
+cudaError_t allow_max_smem_fast() {
+    cudaError_t e = allow_max_smem(fsi_tile_fast_kernel<Acc, 1>);
+    if (e == cudaSuccess) e = allow_max_smem(fsi_tile_fast_kernel<Acc, 2>);
+    if (e == cudaSuccess) e = allow_max_smem(fsi_tile_fast_kernel<Acc, 3>);
+    return e;
 }
 
 template <typename Acc>
@@ -768,7 +839,7 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
                            cudaEvent_t ev2 = nullptr) {
     // every table a kernel of this plan will read must be in place
     const bool exact = TileTraits<Acc>::exact;
-    if (!p.d_tasks || !p.d_Y || !p.d_err || (p.fast12 && (!p.d_fast_tab || !p.d_gtab)) ||
+    if (!p.d_tasks || !p.d_Y || !p.d_err || (p.fast12 && !p.d_gtab) ||
         (!p.mob_only && !p.fast12 && !p.d_trans) ||
         (exact && (!p.d_wnum || !p.d_wden || !p.d_exp)) ||
         (!exact && sizeof(Acc) == 8 && !p.d_wf64) || (!exact && sizeof(Acc) == 4 && !p.d_wf32))
@@ -813,42 +884,17 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
         dim3 g1((unsigned)(1u << p.h), (unsigned)nb);
         if (ev0 && g0 == 0) cudaEventRecord(ev0, st);
         if (p.fast12) {
-            FastArgs fa{};
+            FastArgs fa = fast_args(p);
             fa.v = v;
             fa.G = p.d_Y;
             fa.tile_exp = p.d_exp;
             fa.err = p.d_err;
-            fa.tab = p.d_fast_tab;
-            fa.gtab = p.d_gtab;
-            fa.wnum = p.d_wnum;
-            fa.wden = p.d_wden;
-            fa.wf64 = p.d_wf64;
-            fa.wf32 = p.d_wf32;
-            fa.n_tab = (int)p.fast_tab.size();
-            fa.n_g = p.n_g;
-            fa.off_rec2 = p.off_rec2;
-            fa.off_items2 = p.off_items2;
-            fa.off_rec3 = p.off_rec3;
-            fa.off_items3 = p.off_items3;
-            fa.n_items2 = p.n_items2;
-            fa.n_items3 = p.n_items3;
-            fa.d = p.d;
-            fa.h = p.h;
-            fa.n_ch = p.n_ch;
-            fa.ell = p.ell;
-            fa.prec_bits = p.prec_bits;
-            fa.regA = p.fast_regA;
-            fa.regB = p.fast_regB;
-            fa.load_mask = (1 << p.load_bits) - 1;
-            fa.n_rounds = p.n_rounds;
-            for (int r = 0; r < 4; ++r) {
-                fa.i2_beg[r] = p.i2_beg[r];
-                fa.i2_end[r] = p.i2_end[r];
-                fa.i3_beg[r] = p.i3_beg[r];
-                fa.i3_end[r] = p.i3_end[r];
-            }
             fa.game0 = g0;
-            fsi_tile_fast_kernel<Acc><<<g1, kTileThreads, p.smem_fast, st>>>(fa);
+            switch (p.ell) {
+                case 1: fsi_tile_fast_kernel<Acc, 1><<<g1, kTileThreads, p.smem_fast, st>>>(fa); break;
+                case 2: fsi_tile_fast_kernel<Acc, 2><<<g1, kTileThreads, p.smem_fast, st>>>(fa); break;
+                default: fsi_tile_fast_kernel<Acc, 3><<<g1, kTileThreads, p.smem_fast, st>>>(fa); break;
+            }
         } else {
             fsi_tile_kernel<Acc><<<g1, kTileThreads, p.smem_tile, st>>>(ta);
         }
@@ -977,11 +1023,11 @@ tt_fsi_status tt_fsi_plan_create(int d, int ell, tt_fsi_arith arith, int64_t max
         if (p.fast12) {
             const int fsm = (int)p.smem_fast;
             if (arith == TT_FSI_ARITH_EXACT)
-                e = allow_max_smem(fsi_tile_fast_kernel<long long>);
+                e = allow_max_smem_fast<long long>();
             else if (arith == TT_FSI_ARITH_F64)
-                e = allow_max_smem(fsi_tile_fast_kernel<double>);
+                e = allow_max_smem_fast<double>();
             else
-                e = allow_max_smem(fsi_tile_fast_kernel<float>);
+                e = allow_max_smem_fast<float>();
             if (e != cudaSuccess) {
                 st = cuda_status(e);
                 break;
@@ -1202,7 +1248,7 @@ extern "C" tt_fsi_status tt_fsi_apply_noalloc(int d, int ell, const double *v_de
         void *ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return TT_FSI_ERR_CUDA;
         if (allow_max_smem(fsi_tile_kernel<long long>) != cudaSuccess ||
-            allow_max_smem(fsi_tile_fast_kernel<long long>) != cudaSuccess)
+            allow_max_smem_fast<long long>() != cudaSuccess)
             return TT_FSI_ERR_CUDA;
         g_na_base[dev] = static_cast<unsigned char *>(ptr);
     }
@@ -1292,7 +1338,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) fsi_batch_kernel(BatchArgs a)
             fa.tile_exp = a.tile_exp + g.exp_off;
             fa.err = a.err;
             for (int t = it.first; t < it.first + it.count; ++t) {
-                tile_fast_body<Acc>(fa, 0, t);
+                tile_fast_dispatch<Acc>(fa, 0, t);
                 __syncthreads();
             }
             __threadfence();
@@ -1506,36 +1552,7 @@ tt_fsi_status tt_fsi_batch_create(const tt_fsi_game *games_host, int64_t n_games
     for (size_t i = 0; i < b->plans.size(); ++i) {
         const Plan &p = b->plans[i]->p;
         FastArgs &fa = fpl[i];
-        fa = FastArgs{};
-        fa.tab = p.d_fast_tab;
-        fa.gtab = p.d_gtab;
-        fa.wnum = p.d_wnum;
-        fa.wden = p.d_wden;
-        fa.wf64 = p.d_wf64;
-        fa.wf32 = p.d_wf32;
-        fa.n_tab = (int)p.fast_tab.size();
-        fa.n_g = p.n_g;
-        fa.off_rec2 = p.off_rec2;
-        fa.off_items2 = p.off_items2;
-        fa.off_rec3 = p.off_rec3;
-        fa.off_items3 = p.off_items3;
-        fa.n_items2 = p.n_items2;
-        fa.n_items3 = p.n_items3;
-        fa.d = p.d;
-        fa.h = p.h;
-        fa.n_ch = p.n_ch;
-        fa.ell = p.ell;
-        fa.prec_bits = p.prec_bits;
-        fa.regA = p.fast_regA;
-        fa.regB = p.fast_regB;
-        fa.load_mask = (1 << p.load_bits) - 1;
-        fa.n_rounds = p.n_rounds;
-        for (int r = 0; r < 4; ++r) {
-            fa.i2_beg[r] = p.i2_beg[r];
-            fa.i2_end[r] = p.i2_end[r];
-            fa.i3_beg[r] = p.i3_beg[r];
-            fa.i3_end[r] = p.i3_end[r];
-        }
+        fa = fast_args(p);
         CombineFastArgs &ca = cpl[i];
         ca = CombineFastArgs{};
         ca.tasks = p.d_tasks;

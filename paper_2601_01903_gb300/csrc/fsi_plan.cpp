@@ -17,6 +17,7 @@
 // a(S) of Eq. fsi_closed.  omega is exact rational; the exact path scales
 // each omega_s by the common denominator of its entries.
 #include "fsi_plan.h"
+#include "fast_layout.h"
 
 #include <algorithm>
 #include <cmath>
@@ -224,107 +225,21 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
         p.n_ch = 1 << b;
     }
 
-    // fast tile path tables (see fsi_plan.h)
+    // fast tile path: shared-memory regions of fast_layout.h
     if (want_fast) {
-        // level-k states (sigma, j), grouped into rounds by r = |sigma n bits 0..3|
-        auto states_at = [&](int k) {
-            std::vector<std::tuple<int, uint32_t, int>> st;  // (round, sigma, j)
-            for (uint32_t sg = 0; sg < (1u << k); ++sg) {
-                int s = popc64(sg);
-                if (s > ell) continue;
-                for (int j = 0; j <= k - s; ++j) st.push_back({popc64(sg & 15u), sg, j});
-            }
-            std::sort(st.begin(), st.end());
-            return st;
-        };
-        auto st4 = states_at(4), st8 = states_at(8);
-        const int R = std::min(ell, 4) + 1;  // rounds r = 0..min(l, 4)
-        std::vector<int> first4(R + 1, (int)st4.size()), first8(R + 1, (int)st8.size());
-        for (int r = R - 1; r >= 0; --r) {
-            for (size_t i = 0; i < st4.size(); ++i)
-                if (std::get<0>(st4[i]) == r) { first4[r] = (int)i; break; }
-            for (size_t i = 0; i < st8.size(); ++i)
-                if (std::get<0>(st8[i]) == r) { first8[r] = (int)i; break; }
-            first4[r] = std::min(first4[r], first4[r + 1]);
-            first8[r] = std::min(first8[r], first8[r + 1]);
-        }
-        std::vector<int> b4(16, -1), b8(256, -1);  // relative to the round's first state
-        for (size_t i = 0; i < st4.size(); ++i)
-            if (std::get<2>(st4[i]) == 0) b4[std::get<1>(st4[i])] = (int)i - first4[std::get<0>(st4[i])];
-        for (size_t i = 0; i < st8.size(); ++i)
-            if (std::get<2>(st8[i]) == 0) b8[std::get<1>(st8[i])] = (int)i - first8[std::get<0>(st8[i])];
-        std::vector<int> b12(4096, -1);
-        for (size_t i = 0; i < cur.size(); ++i)
-            if (cur[i].second == 0) b12[cur[i].first] = (int)i;
-        int max4 = 0, max8 = 0;
-        for (int r = 0; r < R; ++r) {
-            max4 = std::max(max4, first4[r + 1] - first4[r]);
-            max8 = std::max(max8, first8[r + 1] - first8[r]);
-        }
-        p.n4 = max4;
-        p.n8 = max8;
-        std::vector<int32_t> &T = p.fast_tab;
-        T.assign(b4.begin(), b4.end());
-        // block 2: records per sigma1 (4 bits), items grouped by round r = |sigma1|
-        std::vector<int32_t> recs2, items2, recs3, items3;
-        std::vector<std::vector<int32_t>> it2(R);
-        int q = 0;
-        for (int r = 0; r < R; ++r)
-            for (uint32_t sg = 0; sg < 16; ++sg) {
-                if (popc64(sg) != r || b4[sg] < 0) continue;
-                recs2.push_back(r);
-                recs2.push_back(b4[sg]);
-                for (uint32_t sr = 0; sr < 16; ++sr) recs2.push_back(b8[sg | (sr << 4)]);
-                for (int u = r; u <= 8; ++u) it2[r].push_back((q << 8) | u);
-                ++q;
-            }
-        // block 3: records per sigma (8 bits), items grouped by (round, |sigma|)
-        std::vector<std::vector<std::vector<int32_t>>> it3(R, std::vector<std::vector<int32_t>>(ell + 1));
-        q = 0;
-        for (int r = 0; r < R; ++r)
-            for (uint32_t sg = 0; sg < 256; ++sg) {
-                if (popc64(sg & 15u) != r || b8[sg] < 0) continue;
-                const int s = popc64(sg);
-                recs3.push_back(s);
-                recs3.push_back(b8[sg]);
-                for (uint32_t sr = 0; sr < 16; ++sr) recs3.push_back(b12[sg | (sr << 8)]);
-                for (int u = s; u <= 12; ++u) it3[r][s].push_back((q << 8) | u);
-                ++q;
-            }
-        for (int r = 0; r < 4; ++r) p.i2_beg[r] = p.i2_end[r] = p.i3_beg[r] = p.i3_end[r] = 0;
-        for (int r = 0; r < R; ++r) {
-            p.i2_beg[r] = (int)items2.size();
-            items2.insert(items2.end(), it2[r].begin(), it2[r].end());
-            while (items2.size() % 2) items2.push_back(-1);
-            p.i2_end[r] = (int)items2.size();
-            p.i3_beg[r] = (int)items3.size();
-            for (auto &grp : it3[r]) {
-                if (grp.empty()) continue;
-                items3.insert(items3.end(), grp.begin(), grp.end());
-                while (items3.size() % 32) items3.push_back(-1);
-            }
-            p.i3_end[r] = (int)items3.size();
-        }
-        p.n_rounds = R;
-        p.off_rec2 = (int)T.size();
-        T.insert(T.end(), recs2.begin(), recs2.end());
-        p.off_items2 = (int)T.size();
-        T.insert(T.end(), items2.begin(), items2.end());
-        p.off_rec3 = (int)T.size();
-        T.insert(T.end(), recs3.begin(), recs3.end());
-        p.off_items3 = (int)T.size();
-        T.insert(T.end(), items3.begin(), items3.end());
-        p.n_items2 = (int)items2.size();
-        p.n_items3 = (int)items3.size();
-        p.fast_regA = std::max(1 << b, p.n8 * 16);
-        p.fast_regB = p.n4 * 256;
+        if (fast::n_chan(ell) != p.n_ch) return TT_FSI_ERR_UNSUPPORTED;  // layouts disagree
+        p.fast_regA = fast::regA_elems(ell);
+        p.fast_regB = fast::regB_elems(ell);
         p.smem_fast = (size_t)(p.fast_regA + p.fast_regB + p.n_ch) * elem;
         p.fast12 = p.smem_fast <= smem_budget;
     }
 
     // channel base of each low set S_L: index of (S_L, j = 0)
     std::map<uint32_t, int> ch_base;
-    if (!p.mob_only) {
+    if (p.fast12) {
+        for (auto &st : cur)
+            if (st.second == 0) ch_base[st.first] = fast::channel_base(ell, (int)st.first);
+    } else if (!p.mob_only) {
         for (size_t i = 0; i < cur.size(); ++i)
             if (cur[i].second == 0) ch_base[cur[i].first] = (int)i;
     }
@@ -346,21 +261,25 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
         p.tasks[i * 4 + 3] = 0;
     }
     if (p.fast12) {
-        // partial-score entries (S_L, s, i), S_L in channel order
+        // partial-score entries (S_L, s, i), ordered by (|S_L|, s, channel, i):
+        // a warp's entries share |S_L| (the length of their sums) and the i of
+        // one (S_L, s) are consecutive, as the combine expects
+        std::vector<std::pair<int, uint32_t>> lows;  // (channel base, S_L)
+        for (auto &kv : ch_base) lows.push_back({kv.second, kv.first});
+        std::sort(lows.begin(), lows.end());
         std::map<std::pair<uint32_t, int>, int> g_of;
         p.gtab.clear();
-        for (size_t c = 0; c < cur.size(); ++c) {
-            if (cur[c].second != 0) continue;
-            const uint32_t SL = cur[c].first;
-            const int sL = popc64(SL);
-            for (int sv = sL; sv <= std::min(ell, sL + p.h); ++sv) {
-                g_of[{SL, sv}] = (int)(p.gtab.size() / 2);
-                for (int i = 0; i <= sv - sL; ++i) {
-                    p.gtab.push_back((int32_t)c);
-                    p.gtab.push_back(sL | (sv << 8) | (i << 16));
+        for (int sL = 0; sL <= ell; ++sL)
+            for (int sv = sL; sv <= ell; ++sv)
+                for (auto &lw : lows) {
+                    const uint32_t SL = lw.second;
+                    if (popc64(SL) != sL || sv > sL + p.h) continue;
+                    g_of[{SL, sv}] = (int)(p.gtab.size() / 2);
+                    for (int i = 0; i <= sv - sL; ++i) {
+                        p.gtab.push_back((int32_t)lw.first);
+                        p.gtab.push_back(sL | (sv << 8) | (i << 16));
+                    }
                 }
-            }
-        }
         p.n_g = (int)(p.gtab.size() / 2);
         for (int64_t i = 0; i < p.n_out; ++i) {
             uint64_t S = masks[i];

@@ -50,23 +50,13 @@ struct Plan {
     int buf_elems = 0;            // elements of one ping-pong buffer
 
     // Fast tile path (b = 12, l <= 3): Moebius in registers, ranked sums in
-    // three 4-bit register blocks with absolute-popcount items, run in rounds
-    // by r = |sigma n bits 0..3|.  Table layout (int32): base4[16] |
-    // rec2[][18] | items2[] | rec3[][18] | items3[]; a record is {round r
-    // (block 2) or |sigma| (block 3), base of (sigma, j=0) relative to its
-    // round, base of (sigma u sigma_r, 0) at the next level for each of the 16
-    // sigma_r (relative to the round for level 8, absolute for the channels;
-    // -1 if pruned)}; an item is q << 8 | u, or -1 (idle padding).
+    // three 4-bit groups by absolute rank, run in rounds r = |sigma n bits
+    // 0..3|; every offset is a closed form (fast_layout.h), so the only table
+    // is gtab.  Shared memory: regA (tile, then one round's level-8 states),
+    // regB (one round's level-4 states), then the n_ch channels.
     bool fast12 = false;
-    int n_rounds = 0;                       // rounds r = |sigma n bits 0..3| = 0..min(l, 4)
-    int i2_beg[4] = {0}, i2_end[4] = {0};   // block-2 items of each round
-    int i3_beg[4] = {0}, i3_end[4] = {0};   // block-3 items of each round
     int fast_regA = 0, fast_regB = 0;       // shared-memory regions (elements)
-    std::vector<int32_t> fast_tab;
-    int off_rec2 = 0, off_items2 = 0, off_rec3 = 0, off_items3 = 0;
-    int n_items2 = 0, n_items3 = 0, n4 = 0, n8 = 0;
     size_t smem_fast = 0;
-    int32_t *d_fast_tab = nullptr;
     // Partial scores per tile on the fast path: one entry per (S_L, s, i)
     // (low set, |S|, |U_H n S_H|), gtab = {ch_base, s_L | s << 8 | i << 16}.
     // The combine tasks' 4th field is the entry of (S_L, s, i = 0).
