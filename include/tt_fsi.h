@@ -309,6 +309,33 @@ tt_fsi_status tt_fsi_masked_game_sampled(const tt_fsi_mlp *model, const double *
 tt_fsi_status tt_fsi_plan_check(tt_fsi_plan plan, struct CUstream_st *stream);
 
 /*
+ * Schedule of tt_fsi_apply on the fast path (12-bit tiles, orders l <= 3;
+ * other plans ignore it).  fused = 0 (the default): a tile launch, then a
+ * combine launch (the cross-tile sums of Section 3.3); the tracing of
+ * tt_fsi_plan_profile splits the time between the two.  fused != 0: one
+ * persistent launch runs the tiles and the combine from one work queue,
+ * tiles_per_item tiles or scores_per_item scores per work item (defaults 1
+ * and 64), so that the combine of a game overlaps the tiles of later games;
+ * it saves a launch for small batches but keeps fewer warps on the
+ * latency-bound combine, so on large batches it is the slower of the two.
+ * Results are bitwise identical either way.  Takes effect on the next call;
+ * not thread-safe against a concurrent tt_fsi_apply of the same plan.
+ */
+tt_fsi_status tt_fsi_plan_set_schedule(tt_fsi_plan plan, int fused, int tiles_per_item, int scores_per_item);
+
+/*
+ * Bound on the fused schedule's device wait: a combine item polls at most
+ * `polls` times (about 200 ns apart) for its game's tiles; past it the call
+ * latches TT_FSI_ERR_TIMEOUT (reported by tt_fsi_plan_check), its scores
+ * are left unwritten and every later wait of the launch gives up at once.
+ * The wait always ends well inside the default (4,000,000 polls) unless the
+ * device is broken; the bound exists so that a broken device never hangs.
+ * inject_missing != 0 is a test hook: every wait then expects one tile more
+ * than the game has, so each wait runs out and the timeout path is taken.
+ */
+tt_fsi_status tt_fsi_plan_set_wait_limit(tt_fsi_plan plan, long long polls, int inject_missing);
+
+/*
  * Allocation-free FSI, exact arithmetic.  (This entry point has no
  * counterpart in the paper; it exists for deployment.)
  *

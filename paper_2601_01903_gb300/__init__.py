@@ -109,6 +109,18 @@ class Plan:
     def check(self, stream=None):
         _check(self._lib.tt_fsi_plan_check(self._h, _stream_ptr(stream)), "tt_fsi_plan_check")
 
+    def set_schedule(self, fused: bool = False, tiles_per_item: int = 1, scores_per_item: int = 64):
+        """Tile launch + combine launch (default) or one fused persistent
+        launch (fast path only; results are identical)."""
+        _check(self._lib.tt_fsi_plan_set_schedule(self._h, int(bool(fused)), tiles_per_item,
+                                                  scores_per_item), "tt_fsi_plan_set_schedule")
+
+    def set_wait_limit(self, polls: int, inject_missing: bool = False):
+        """Bound on the fused schedule's device wait; inject_missing makes
+        every wait run out (test hook of the timeout path)."""
+        _check(self._lib.tt_fsi_plan_set_wait_limit(self._h, polls, int(bool(inject_missing))),
+               "tt_fsi_plan_set_wait_limit")
+
 
 def fsi(v, d: int, ell: int, arith: str = "exact"):
     """One-shot FSI of v [B, 2^d] (CUDA tensor)."""

@@ -30,7 +30,7 @@
 
 namespace ttfsi {
 
-enum : int { kErrNonFinite = 1 };
+enum : int { kErrNonFinite = 1, kErrTimeout = 2 };
 
 struct TileArgs {
     const void *v;
@@ -78,7 +78,7 @@ __device__ __forceinline__ long long to_fixed(unsigned long long bits, int E, in
     else if (sh >= 64)
         r = 0;
     else
-        r = (mant + (1ull << (sh - 1))) >> sh;
+        r = ((mant >> (sh - 1)) + 1) >> 1;  // = (mant + 2^(sh-1)) >> sh: round half up
     long long x = (long long)r;
     return (bits >> 63) ? -x : x;
 }
@@ -234,6 +234,8 @@ struct FastArgs {
     const float *wf32;
     int n_g;
     int d, h, ell, prec_bits, load_mask;
+    int g_split31;        // exact weighting by 32 x 32-bit products (see the plan)
+    int prefetch_ahead;   // tile launch: prefetch the tile this many CTAs ahead into L2 (0: off)
     long long game0;
 };
 
@@ -419,6 +421,49 @@ __device__ __forceinline__ void fast_round(const Acc (&x)[16], Acc *regA, Acc *r
     if constexpr (RD < L) fast_round<L, RD + 1>(x, regA, regB, regY, tid, pos);
 }
 
+// One partial score: sum over j < J = 13 - |S_L| of the weight
+// omega_s(p, |S_L| + j) (plus 1 at j = 0 when ident) times the channel
+// Y(S_L, j); wo indexes omega_s(p, |S_L|).  All loads are issued before the
+// products.  Exact path: weights are integer numerators over D_s (the
+// identity term is D_s); with g_split31 every product is two 32 x 32-bit
+// multiply-adds (y = yh 2^31 + yl), else a full 64 x 64 -> 128-bit product.
+template <typename Acc, int J>
+__device__ __forceinline__ typename GTraits<Acc>::G fast_g_entry(const FastArgs &a, const Acc *y, long long wo, int s,
+                                                                bool ident) {
+    using GT = typename GTraits<Acc>::G;
+    Acc yv[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) yv[j] = y[j];
+    if constexpr (TileTraits<Acc>::exact) {
+        long long c[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) c[j] = __ldg(a.wnum + wo + j);
+        if (ident) c[0] += __ldg(a.wden + s);
+        if (a.g_split31) {
+            long long acc_h = 0, acc_l = 0;
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                acc_h += (long long)(int)c[j] * (int)(yv[j] >> 31);
+                acc_l += (long long)(int)c[j] * (int)(yv[j] & 0x7fffffffll);
+            }
+            return (GT)(((unsigned __int128)(__int128)acc_h) << 31) + (GT)acc_l;
+        }
+        GT acc = 0;
+#pragma unroll
+        for (int j = 0; j < J; ++j) acc += mul_wide(yv[j], c[j]);
+        return acc;
+    } else {
+        Acc acc = 0;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            Acc c = (sizeof(Acc) == 4) ? (Acc)__ldg(a.wf32 + wo + j) : (Acc)__ldg(a.wf64 + wo + j);
+            if (j == 0 && ident) c += (Acc)1;
+            acc += yv[j] * c;
+        }
+        return acc;
+    }
+}
+
 template <typename Acc, int L>
 __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long long game, const long long tile) {
     using In = typename TileTraits<Acc>::In;
@@ -488,33 +533,28 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
     // ---- partial scores G(S_L, s, i) of this tile ----
     const int uH = __popcll((unsigned long long)tile);
     const int P1 = a.h + 1, Q1 = 13;
-    GT *gdst = reinterpret_cast<GT *>(a.G) + ((game << a.h) + tile) * (long long)a.n_g;
+    // partial scores of a game are stored entry-major, [n_g][2^h tiles], so
+    // that the combine's lanes (consecutive tiles) read consecutive addresses
+    const long long ntile = 1ll << a.h;
+    GT *gdst = reinterpret_cast<GT *>(a.G) + (game << a.h) * (long long)a.n_g + tile;
     for (int g = tid; g < a.n_g; g += kTileThreads) {
         const int cb = __ldg(a.gtab + 2 * g), code = __ldg(a.gtab + 2 * g + 1);
         const int sL = code & 0xff, s = (code >> 8) & 0xff, i = code >> 16;
         const int r = s - sL, pp = uH + r - i;
         GT acc = 0;
         if (i <= uH && r - i <= a.h - uH) {
-            const Acc *y = regY + cb;
-            const int J = 13 - sL;
-            if constexpr (TileTraits<Acc>::exact) {
-                const long long *w = a.wnum + ((long long)s * P1 + pp) * Q1 + sL;
-                const long long id = (i == uH) ? a.wden[s] : 0ll;
-                for (int j = 0; j < J; ++j) {
-                    const long long c = __ldg(w + j) + (j == 0 ? id : 0ll);
-                    acc += mul_wide(y[j], c);
-                }
-            } else {
-                const long long wo = ((long long)s * P1 + pp) * Q1 + sL;
-                for (int j = 0; j < J; ++j) {
-                    Acc c = (sizeof(Acc) == 4) ? (Acc)__ldg(a.wf32 + wo + j) : (Acc)__ldg(a.wf64 + wo + j);
-                    if (j == 0 && i == uH) c += (Acc)1;
-                    acc += y[j] * c;
-                }
+            // entries are sorted by |S_L|, so a warp almost always takes one case
+            const long long wo = ((long long)s * P1 + pp) * Q1 + sL;
+            const bool ident = (i == uH);
+            switch (sL) {
+                case 0: acc = fast_g_entry<Acc, 13>(a, regY + cb, wo, s, ident); break;
+                case 1: acc = fast_g_entry<Acc, 12>(a, regY + cb, wo, s, ident); break;
+                case 2: acc = fast_g_entry<Acc, 11>(a, regY + cb, wo, s, ident); break;
+                default: acc = fast_g_entry<Acc, 10>(a, regY + cb, wo, s, ident); break;
             }
             if ((r - i) & 1) acc = -acc;
         }
-        gdst[g] = acc;
+        gdst[g * ntile] = acc;
     }
     if constexpr (TileTraits<Acc>::exact) {
         if (tid == 0) a.tile_exp[(game << a.h) + tile] = a.prec_bits + 1022 - E;
@@ -531,8 +571,23 @@ __device__ __forceinline__ void tile_fast_dispatch(const FastArgs &a, const long
     }
 }
 
+// One CTA per (tile, game).  CTAs start roughly in linear order, so each asks
+// L2 to prefetch the input of the tile prefetch_ahead CTAs later (about one
+// wave of resident CTAs), which that CTA will then load from L2, not HBM.
 template <typename Acc, int L>
 __global__ void __launch_bounds__(kTileThreads, 2) fsi_tile_fast_kernel(FastArgs a) {
+    using In = typename TileTraits<Acc>::In;
+    if (a.prefetch_ahead > 0) {
+        const long long lin = (long long)blockIdx.y * gridDim.x + blockIdx.x + a.prefetch_ahead;
+        if (lin < (long long)gridDim.x * gridDim.y) {
+            const long long gy = lin / gridDim.x, gx = lin - gy * gridDim.x;
+            const char *base = reinterpret_cast<const char *>(reinterpret_cast<const In *>(a.v) +
+                                                              ((a.game0 + gy) << a.d) + (gx << fast::kBits));
+            const int bytes = (a.load_mask + 1) * (int)sizeof(In);
+            for (int o = threadIdx.x * 128; o < bytes; o += kTileThreads * 128)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(base + o));
+        }
+    }
     tile_fast_body<Acc, L>(a, a.game0 + blockIdx.y, blockIdx.x);
 }
 
@@ -590,22 +645,38 @@ __device__ __forceinline__ void combine_fast_body(const CombineFastArgs &a, cons
         atomicMax(&s_fmax, fmax);
         __syncthreads();
         const int Fc = min(s_fmax, s_fmin + a.shift_cap);
+        constexpr int U = 8;  // independent loads in flight per lane
         for (long long task = task_begin + warp; task < task_end; task += kCombineFastWarps) {
             const unsigned SH = (unsigned)a.tasks[task * 4 + 1];
             const int s = a.tasks[task * 4 + 2] & 0xff;
-            const int gb = a.tasks[task * 4 + 3];
+            const GT *Gs = Gg + (long long)a.tasks[task * 4 + 3] * ntile;
             __int128 acc = 0;
-            for (int u = lane; u < ntile; u += 32) {
-                const GT *gp = Gg + (long long)u * a.n_g + gb + __popc((unsigned)u & SH);
-                const longlong2 raw = __ldcg(reinterpret_cast<const longlong2 *>(gp));
-                __int128 g = (__int128)(((unsigned __int128)(unsigned long long)raw.y << 64) |
-                                        (unsigned long long)raw.x);
-                const int delta = Fc - __ldcg(texp + u);
-                if (delta >= 0)
-                    g = (__int128)((unsigned __int128)g << delta);
-                else
-                    g = (-delta >= 127) ? (__int128)0 : ((g + ((__int128)1 << (-delta - 1))) >> (-delta));
-                acc += g;
+            for (int u0 = lane; u0 < ntile; u0 += 32 * U) {
+                longlong2 raw[U];
+                int f[U];
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    const int u = u0 + 32 * k;
+                    if (u < ntile) {
+                        raw[k] = __ldcg(reinterpret_cast<const longlong2 *>(
+                            Gs + (long long)__popc((unsigned)u & SH) * ntile + u));
+                        f[k] = __ldcg(texp + u);
+                    } else {
+                        raw[k] = make_longlong2(0, 0);
+                        f[k] = Fc;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    __int128 g = (__int128)(((unsigned __int128)(unsigned long long)raw[k].y << 64) |
+                                            (unsigned long long)raw[k].x);
+                    const int delta = Fc - f[k];
+                    if (delta >= 0)
+                        g = (__int128)((unsigned __int128)g << delta);
+                    else
+                        g = (-delta >= 127) ? (__int128)0 : ((g + ((__int128)1 << (-delta - 1))) >> (-delta));
+                    acc += g;
+                }
             }
             for (int o = 16; o > 0; o >>= 1) acc += shfl_down_i128(acc, o);
             if (lane == 0) {
@@ -614,12 +685,21 @@ __device__ __forceinline__ void combine_fast_body(const CombineFastArgs &a, cons
             }
         }
     } else {
+        constexpr int U = 8;
         for (long long task = task_begin + warp; task < task_end; task += kCombineFastWarps) {
             const unsigned SH = (unsigned)a.tasks[task * 4 + 1];
-            const int gb = a.tasks[task * 4 + 3];
+            const GT *Gs = Gg + (long long)a.tasks[task * 4 + 3] * ntile;
             Acc acc = 0;
-            for (int u = lane; u < ntile; u += 32)
-                acc += __ldcg(Gg + (long long)u * a.n_g + gb + __popc((unsigned)u & SH));
+            for (int u0 = lane; u0 < ntile; u0 += 32 * U) {
+                Acc part[U];
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    const int u = u0 + 32 * k;
+                    part[k] = (u < ntile) ? __ldcg(Gs + (long long)__popc((unsigned)u & SH) * ntile + u) : (Acc)0;
+                }
+#pragma unroll
+                for (int k = 0; k < U; ++k) acc += part[k];
+            }
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
             if (lane == 0) reinterpret_cast<Acc *>(a.phi)[game * a.n_out + task] = acc;
         }
@@ -631,6 +711,117 @@ __global__ void __launch_bounds__(32 * kCombineFastWarps) fsi_combine_fast_kerne
     const long long t0 = (long long)blockIdx.x * kCombineFastWarps;
     const long long t1 = (t0 + kCombineFastWarps < a.n_out) ? t0 + kCombineFastWarps : a.n_out;
     combine_fast_body<Acc>(a, a.game0 + blockIdx.y, t0, t1);
+}
+
+// ----------------------------------------------------------------------------
+// Fused apply of a fast-path plan: one persistent launch runs the tiles and
+// the combine of all B games.  Work items come from a device counter in the
+// order T(0), T(1), S(0), T(2), S(1), ..., T(B-1), S(B-2), S(B-1), where T(g)
+// are the tiles of game g (tiles_per_item at a time) and S(g) its score
+// chunks, so the combine of a game runs beside the tiles of later games.  A
+// score chunk waits until every tile of its game is done; those tiles were
+// handed out earlier to running CTAs that never wait, so the wait ends, and
+// it is bounded all the same (spin_limit polls, then kErrTimeout is latched
+// and every later wait gives up at once).  A CTA that takes a tile item asks
+// L2 to prefetch the input of the item one grid width ahead, which hides most
+// of the HBM latency of the next tile's load.
+// ----------------------------------------------------------------------------
+struct ApplyArgs {
+    FastArgs fa;
+    CombineFastArgs ca;
+    int B, n_tiles, tpi, spi, nt, ns;  // games, tiles per game, tiles / scores per item, items per game
+    long long n_items;
+    int *counters;                     // [0] queue head, [1 + g] finished tiles of game g
+    long long spin_limit;
+    int inject_missing;                // test hook: every wait expects one tile more than exists
+};
+
+struct ApplyItem {
+    int tile, game, first, count;
+};
+
+__device__ __forceinline__ ApplyItem apply_item(const ApplyArgs &a, long long k) {
+    ApplyItem it;
+    int r;
+    if (k < a.nt) {
+        it.tile = 1;
+        it.game = 0;
+        r = (int)k;
+    } else {
+        const long long per = a.nt + a.ns, kk = k - a.nt, blk = kk / per;
+        const int rr = (int)(kk - blk * per);
+        if (blk < a.B - 1) {
+            it.tile = rr < a.nt;
+            it.game = it.tile ? (int)blk + 1 : (int)blk;
+            r = it.tile ? rr : rr - a.nt;
+        } else {
+            it.tile = 0;
+            it.game = a.B - 1;
+            r = (int)(kk - (long long)(a.B - 1) * per);
+        }
+    }
+    if (it.tile) {
+        it.first = r * a.tpi;
+        it.count = min(a.tpi, a.n_tiles - it.first);
+    } else {
+        it.first = r * a.spi;
+        it.count = (int)min((long long)a.spi, a.ca.n_out - it.first);
+    }
+    return it;
+}
+
+template <typename Acc, int L>
+__global__ void __launch_bounds__(kTileThreads, 2) fsi_apply_fast_kernel(ApplyArgs a) {
+    using In = typename TileTraits<Acc>::In;
+    __shared__ long long s_item;
+    __shared__ int s_ok;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(a.counters, 1);
+        __syncthreads();
+        const long long item = s_item;
+        __syncthreads();
+        if (item >= a.n_items) break;
+        const ApplyItem it = apply_item(a, item);
+        if (it.tile) {
+            const long long ahead = item + gridDim.x;
+            if (ahead < a.n_items) {
+                const ApplyItem pf = apply_item(a, ahead);
+                if (pf.tile) {
+                    const char *base = reinterpret_cast<const char *>(
+                        reinterpret_cast<const In *>(a.fa.v) + ((long long)pf.game << a.fa.d) +
+                        ((long long)pf.first << fast::kBits));
+                    const long long bytes = (long long)pf.count * (a.fa.load_mask + 1) * (long long)sizeof(In);
+                    for (long long o = threadIdx.x * 128ll; o < bytes; o += kTileThreads * 128ll)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(base + o));
+                }
+            }
+            for (int t = it.first; t < it.first + it.count; ++t) {
+                tile_fast_body<Acc, L>(a.fa, it.game, t);
+                __syncthreads();
+            }
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) atomicAdd(a.counters + 1 + it.game, it.count);
+        } else {
+            if (threadIdx.x == 0) {
+                int ok = 1;
+                long long polls = 0;
+                while (atomicAdd(a.counters + 1 + it.game, 0) < a.n_tiles + a.inject_missing) {
+                    if ((atomicAdd(a.fa.err, 0) & kErrTimeout) || ++polls > a.spin_limit) {
+                        atomicOr(a.fa.err, kErrTimeout);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(200);
+                }
+                __threadfence();
+                s_ok = ok;
+            }
+            __syncthreads();
+            if (s_ok) combine_fast_body<Acc>(a.ca, it.game, it.first, it.first + it.count);
+            __syncthreads();
+        }
+    }
 }
 
 // ----------------------------------------------------------------------------
@@ -805,6 +996,7 @@ void free_plan_device(Plan *p) {
     cudaFree(p->d_exp);
     cudaFree(p->d_err);
     cudaFree(p->d_gtab);
+    cudaFree(p->d_counters);
 }
 
 // Kernel arguments of a fast-path plan that do not depend on the call.
@@ -821,15 +1013,49 @@ FastArgs fast_args(const Plan &p) {
     fa.ell = p.ell;
     fa.prec_bits = p.prec_bits;
     fa.load_mask = (1 << p.load_bits) - 1;
+    fa.g_split31 = p.g_split31 ? 1 : 0;
     return fa;
 }
 
-// Raises the shared-memory cap of every order's fast tile kernel.
+// Kernel arguments of the fast combine that do not depend on the call.
+CombineFastArgs combine_fast_args(const Plan &p) {
+    CombineFastArgs cf{};
+    cf.G = p.d_Y;
+    cf.tile_exp = p.d_exp;
+    cf.tasks = p.d_tasks;
+    cf.wden = p.d_wden;
+    cf.h = p.h;
+    cf.n_g = p.n_g;
+    cf.shift_cap = p.shift_cap;
+    cf.n_out = p.n_out;
+    return cf;
+}
+
+// Raises the shared-memory cap of every order's fast tile and fused kernels.
 template <typename Acc>
 cudaError_t allow_max_smem_fast() {
     cudaError_t e = allow_max_smem(fsi_tile_fast_kernel<Acc, 1>);
     if (e == cudaSuccess) e = allow_max_smem(fsi_tile_fast_kernel<Acc, 2>);
     if (e == cudaSuccess) e = allow_max_smem(fsi_tile_fast_kernel<Acc, 3>);
+    if (e == cudaSuccess) e = allow_max_smem(fsi_apply_fast_kernel<Acc, 1>);
+    if (e == cudaSuccess) e = allow_max_smem(fsi_apply_fast_kernel<Acc, 2>);
+    if (e == cudaSuccess) e = allow_max_smem(fsi_apply_fast_kernel<Acc, 3>);
+    return e;
+}
+
+// Persistent grid of the fused kernel: SMs x resident CTAs per SM.
+template <typename Acc>
+cudaError_t fused_grid(const Plan &p, int *grid) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    switch (p.ell) {
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fsi_apply_fast_kernel<Acc, 1>, kTileThreads, p.smem_fast); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fsi_apply_fast_kernel<Acc, 2>, kTileThreads, p.smem_fast); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fsi_apply_fast_kernel<Acc, 3>, kTileThreads, p.smem_fast); break;
+    }
+    *grid = std::max(1, occ) * sms;
     return e;
 }
 
@@ -876,6 +1102,41 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
     ca.shift_cap = p.shift_cap;
     ca.mob_only = ta.mob_only;
     ca.n_out = p.n_out;
+    if (p.fast12 && p.fused) {
+        if (!p.d_counters || p.apply_grid < 1) return TT_FSI_ERR_INVALID_ARG;
+        ApplyArgs aa{};
+        aa.fa = fast_args(p);
+        aa.fa.v = v;
+        aa.fa.G = p.d_Y;
+        aa.fa.tile_exp = p.d_exp;
+        aa.fa.err = p.d_err;
+        aa.ca = combine_fast_args(p);
+        aa.ca.phi = phi;
+        aa.B = (int)B;
+        aa.n_tiles = 1 << p.h;
+        aa.tpi = p.tiles_per_item;
+        aa.spi = p.scores_per_item;
+        aa.nt = (aa.n_tiles + aa.tpi - 1) / aa.tpi;
+        aa.ns = (int)((p.n_out + aa.spi - 1) / aa.spi);
+        aa.n_items = (long long)B * (aa.nt + aa.ns);
+        aa.counters = p.d_counters;
+        aa.spin_limit = p.spin_limit;
+        aa.inject_missing = p.inject_missing ? 1 : 0;
+        const unsigned grid = (unsigned)std::min<long long>(aa.n_items, p.apply_grid);
+        if (ev0) cudaEventRecord(ev0, st);
+        cudaError_t e = cudaMemsetAsync(p.d_counters, 0, (size_t)(B + 1) * sizeof(int), st);
+        if (e != cudaSuccess) return cuda_status(e);
+        switch (p.ell) {
+            case 1: fsi_apply_fast_kernel<Acc, 1><<<grid, kTileThreads, p.smem_fast, st>>>(aa); break;
+            case 2: fsi_apply_fast_kernel<Acc, 2><<<grid, kTileThreads, p.smem_fast, st>>>(aa); break;
+            default: fsi_apply_fast_kernel<Acc, 3><<<grid, kTileThreads, p.smem_fast, st>>>(aa); break;
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_status(e);
+        if (ev1) cudaEventRecord(ev1, st);
+        if (ev2) cudaEventRecord(ev2, st);
+        return TT_FSI_OK;
+    }
     const int64_t chunk = 65535;
     for (int64_t g0 = 0; g0 < B; g0 += chunk) {
         const int nb = (int)((B - g0 < chunk) ? (B - g0) : chunk);
@@ -890,6 +1151,7 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
             fa.tile_exp = p.d_exp;
             fa.err = p.d_err;
             fa.game0 = g0;
+            fa.prefetch_ahead = p.apply_grid;
             switch (p.ell) {
                 case 1: fsi_tile_fast_kernel<Acc, 1><<<g1, kTileThreads, p.smem_fast, st>>>(fa); break;
                 case 2: fsi_tile_fast_kernel<Acc, 2><<<g1, kTileThreads, p.smem_fast, st>>>(fa); break;
@@ -1021,13 +1283,21 @@ tt_fsi_status tt_fsi_plan_create(int d, int ell, tt_fsi_arith arith, int64_t max
             break;
         }
         if (p.fast12) {
-            const int fsm = (int)p.smem_fast;
             if (arith == TT_FSI_ARITH_EXACT)
                 e = allow_max_smem_fast<long long>();
             else if (arith == TT_FSI_ARITH_F64)
                 e = allow_max_smem_fast<double>();
             else
                 e = allow_max_smem_fast<float>();
+            if (e == cudaSuccess) {
+                if (arith == TT_FSI_ARITH_EXACT)
+                    e = fused_grid<long long>(p, &p.apply_grid);
+                else if (arith == TT_FSI_ARITH_F64)
+                    e = fused_grid<double>(p, &p.apply_grid);
+                else
+                    e = fused_grid<float>(p, &p.apply_grid);
+            }
+            if (e == cudaSuccess) e = cudaMalloc((void **)&p.d_counters, (size_t)(max_batch + 1) * sizeof(int));
             if (e != cudaSuccess) {
                 st = cuda_status(e);
                 break;
@@ -1148,7 +1418,23 @@ tt_fsi_status tt_fsi_plan_check(tt_fsi_plan plan, struct CUstream_st *stream) {
     if (e == cudaSuccess) e = cudaMemsetAsync(plan->p.d_err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(e);
+    if (h_err & kErrTimeout) return TT_FSI_ERR_TIMEOUT;
     if (h_err & kErrNonFinite) return TT_FSI_ERR_NONFINITE;
+    return TT_FSI_OK;
+}
+
+tt_fsi_status tt_fsi_plan_set_schedule(tt_fsi_plan plan, int fused, int tiles_per_item, int scores_per_item) {
+    if (!plan || tiles_per_item < 1 || scores_per_item < 1) return TT_FSI_ERR_INVALID_ARG;
+    plan->p.fused = fused != 0;
+    plan->p.tiles_per_item = tiles_per_item;
+    plan->p.scores_per_item = scores_per_item;
+    return TT_FSI_OK;
+}
+
+tt_fsi_status tt_fsi_plan_set_wait_limit(tt_fsi_plan plan, long long polls, int inject_missing) {
+    if (!plan || polls < 0) return TT_FSI_ERR_INVALID_ARG;
+    plan->p.spin_limit = polls;
+    plan->p.inject_missing = inject_missing != 0;
     return TT_FSI_OK;
 }
 
@@ -1238,6 +1524,8 @@ extern "C" tt_fsi_status tt_fsi_apply_noalloc(int d, int ell, const double *v_de
     off = align256(off + (size_t)B * ntile * sizeof(int));
     const size_t o_Y = off;
     off = align256(off + (size_t)B * tile_out_bytes_per_game(p));
+    const size_t o_cnt = off;
+    off = align256(off + (size_t)(B + 1) * sizeof(int));
     if (off > kNoAllocBytes) return TT_FSI_ERR_UNSUPPORTED;  // beyond the 64 MiB array
 
     // once per device: the array's device address (with that device current)
@@ -1252,6 +1540,8 @@ extern "C" tt_fsi_status tt_fsi_apply_noalloc(int d, int ell, const double *v_de
             return TT_FSI_ERR_CUDA;
         g_na_base[dev] = static_cast<unsigned char *>(ptr);
     }
+    if (p.fast12 && p.apply_grid == 0 && fused_grid<long long>(p, &p.apply_grid) != cudaSuccess)
+        return TT_FSI_ERR_CUDA;
     unsigned char *base = g_na_base[dev];
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
@@ -1266,6 +1556,7 @@ extern "C" tt_fsi_status tt_fsi_apply_noalloc(int d, int ell, const double *v_de
     p.d_err = reinterpret_cast<int *>(base);
     p.d_exp = reinterpret_cast<int *>(base + o_exp);
     p.d_Y = base + o_Y;
+    p.d_counters = reinterpret_cast<int *>(base + o_cnt);
     tt_fsi_status s = launch_apply<long long>(p, v_dev, B, phi_dev, st);
     if (s != TT_FSI_OK) return s;
     noalloc_poison_kernel<<<64, 256, 0, st>>>(p.d_err, phi_dev, (long long)B * p.n_out);
@@ -1288,8 +1579,6 @@ extern "C" tt_fsi_status tt_fsi_apply_noalloc(int d, int ell, const double *v_de
 
 namespace ttfsi {
 namespace {
-
-enum : int { kErrTimeout = 2 };
 
 struct BatchGameDev {
     long long v_off, phi_off, g_off, exp_off;  // element offsets into v, phi, partial scores, exponents

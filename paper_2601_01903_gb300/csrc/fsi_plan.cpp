@@ -350,6 +350,26 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
     // denominator it must stay below 2^126.
     p.shift_cap = 124 - p.ell_eff - p.prec_bits - max_den_bits;
     p.shift_cap = std::max(0, std::min(p.shift_cap, 60));
+
+    // Split-product weighting on the fast exact path: a channel Y (|Y| <=
+    // 3^12 2^P) is split as Y = Yh 2^31 + Yl, 0 <= Yl < 2^31, so that each
+    // weight c times Yh and times Yl is one 32 x 32 -> 64-bit multiply-add.
+    // Valid when both int64 sums of at most 13 terms cannot overflow and Yh
+    // fits in int32; the weight includes the identity term D_s of j = 0.
+    p.g_split31 = false;
+    if (p.fast12 && arith == TT_FSI_ARITH_EXACT) {
+        long long cmax = 0;
+        for (int s = 0; s < S1; ++s)
+            for (int pp = 0; pp < P1; ++pp)
+                for (int q = 0; q < Q1; ++q) {
+                    const long long c = p.wnum[((size_t)s * P1 + pp) * Q1 + q];
+                    cmax = std::max(cmax, (c < 0 ? -c : c) + p.wden[s]);
+                }
+        const __int128 ymax = (__int128)531441 << p.prec_bits;  // 3^12 2^P
+        const __int128 yh_max = (ymax >> 31) + 1, lim = (__int128)1 << 63;
+        p.g_split31 = cmax < (1ll << 31) && yh_max < ((__int128)1 << 31) &&
+                      (__int128)13 * cmax * ((__int128)1 << 31) < lim && (__int128)13 * cmax * yh_max < lim;
+    }
     return TT_FSI_OK;
 }
 

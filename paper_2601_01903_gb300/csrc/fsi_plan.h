@@ -41,6 +41,7 @@ struct Plan {
     int64_t n_out = 0;        // scores per game
     int n_ch = 0;             // channels per tile (states at the last level)
     int prec_bits = 0;        // fixed-point headroom P of the exact path
+    bool g_split31 = false;   // fast exact path: weights small enough for 32 x 32-bit products
     int shift_cap = 0;        // largest exponent gap aligned exactly across tiles
 
     // ranked superset sums: states per level and (src for tau=0, src for tau=1)
@@ -57,6 +58,15 @@ struct Plan {
     bool fast12 = false;
     int fast_regA = 0, fast_regB = 0;       // shared-memory regions (elements)
     size_t smem_fast = 0;
+    // Schedule of a fast-path apply: one fused persistent launch (tiles and
+    // combine from one work queue; default) or a tile launch then a combine
+    // launch.  Work-item sizes and the bound on the combine's wait.
+    bool fused = false;
+    int tiles_per_item = 1, scores_per_item = 64;
+    int apply_grid = 0;                     // persistent CTAs (SMs x resident CTAs per SM)
+    long long spin_limit = 4000000;
+    bool inject_missing = false;            // test hook of the bounded wait
+    int *d_counters = nullptr;              // [0] queue head, [1 + g] finished tiles of game g
     // Partial scores per tile on the fast path: one entry per (S_L, s, i)
     // (low set, |S|, |U_H n S_H|), gtab = {ch_base, s_L | s << 8 | i << 16}.
     // The combine tasks' 4th field is the entry of (S_L, s, i = 0).

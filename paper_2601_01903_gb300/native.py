@@ -120,6 +120,10 @@ def _declare(lib):
     lib.tt_fsi_apply.argtypes = [vp, vp, i64, vp, vp]
     lib.tt_fsi_plan_check.restype = i
     lib.tt_fsi_plan_check.argtypes = [vp, vp]
+    lib.tt_fsi_plan_set_schedule.restype = i
+    lib.tt_fsi_plan_set_schedule.argtypes = [vp, i, i, i]
+    lib.tt_fsi_plan_set_wait_limit.restype = i
+    lib.tt_fsi_plan_set_wait_limit.argtypes = [vp, c.c_longlong, i]
     lib.tt_fsi_last_cuda_error.restype = c.c_char_p
     lib.tt_fsi_last_cuda_error.argtypes = []
     lib.tt_fsi_status_string.restype = c.c_char_p

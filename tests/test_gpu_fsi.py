@@ -174,3 +174,51 @@ def test_repeated_calls_are_bitwise_identical():
     a = plan.apply(v).clone()
     b = plan.apply(v).clone()
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("arith", ["exact", "f64", "f32"])
+@pytest.mark.parametrize("d,ell,B", [(14, 3, 5), (20, 2, 2), (9, 3, 7), (16, 1, 3), (13, 3, 1)])
+def test_fused_schedule_matches_two_launches(arith, d, ell, B):
+    """The fused persistent launch and the tile-then-combine launches run the
+    same per-tile and per-score code: results are bitwise identical."""
+    dt = torch.float32 if arith == "f32" else torch.float64
+    v = _gpu(_noise_games(d, B, seed=d + ell), dt)
+    plan = fsi.Plan(d, ell, arith, max_batch=B)
+    split = plan.apply(v).clone()  # default schedule: tile launch + combine launch
+    plan.set_schedule(fused=True)
+    fused = plan.apply(v).clone()
+    plan.check()
+    assert torch.equal(fused, split)
+
+
+@pytest.mark.parametrize("tpi,spi", [(1, 1), (3, 64), (8, 1000), (256, 7)])
+def test_fused_work_item_sizes(oracle_mod, tpi, spi):
+    d, ell, B = 15, 3, 3
+    v = _noise_games(d, B, seed=11)
+    ref = oracle_mod.fsi(v, d, ell)
+    plan = fsi.Plan(d, ell, "exact", max_batch=B)
+    plan.set_schedule(fused=True, tiles_per_item=tpi, scores_per_item=spi)
+    got = plan.apply(_gpu(v)).cpu().numpy()
+    plan.check()
+    assert _rel_err(got, ref, v) <= TOL
+
+
+def test_fused_wait_timeout_is_reported_and_recoverable():
+    """Test hook: every combine wait expects one tile more than exists, so
+    each wait runs out after a short bound; the timeout is latched, read by
+    the host, and the next call with the hook off is correct."""
+    d, ell, B = 14, 2, 2
+    v = _gpu(_noise_games(d, B, seed=3))
+    plan = fsi.Plan(d, ell, "exact", max_batch=B)
+    plan.set_schedule(fused=True)
+    ref = plan.apply(v).clone()
+    plan.check()
+    plan.set_wait_limit(20000, inject_missing=True)
+    plan.apply(v)
+    with pytest.raises(fsi.FsiError) as e:
+        plan.check()
+    assert e.value.status == 5
+    plan.set_wait_limit(4000000, inject_missing=False)
+    again = plan.apply(v)
+    plan.check()
+    assert torch.equal(again, ref)
