@@ -137,19 +137,18 @@ def peaks():
 
 def kernel_traffic():
     """dram bytes per launch of the tile kernel from the committed ncu
-    summary, if the kernel source still matches the one profiled."""
+    summary, if the kernel's source files still match the ones profiled."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             t = json.load(f)
-    except (OSError, ValueError):
+        h = hashlib.sha256()
+        for src in t["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+    except (OSError, ValueError, KeyError):
         return None
-    src = os.path.join(ROOT, t.get("source", ""))
-    try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    except OSError:
-        return None
-    if h != t.get("source_sha256_16"):
+    if h.hexdigest()[:16] != t.get("sources_sha256_16"):
         return None
     return t.get("dram_bytes_per_launch")
 

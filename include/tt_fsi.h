@@ -156,7 +156,7 @@ tt_fsi_status tt_fsi_batch_create(const tt_fsi_game *games_host, int64_t n_games
 void tt_fsi_batch_destroy(tt_fsi_batch batch);
 
 /*
- * FSI of every game of the batch.  Games with l <= 3 and l < d run in ONE
+ * FSI of every game of the batch.  Games with l <= 4 and l < d run in ONE
  * persistent launch (one CTA per SM pulling tiles, then score chunks, from a
  * device work queue; a chunk waits for its game's tiles with a bounded
  * number of polls and reports TT_FSI_ERR_TIMEOUT through
@@ -309,7 +309,7 @@ tt_fsi_status tt_fsi_masked_game_sampled(const tt_fsi_mlp *model, const double *
 tt_fsi_status tt_fsi_plan_check(tt_fsi_plan plan, struct CUstream_st *stream);
 
 /*
- * Schedule of tt_fsi_apply on the fast path (12-bit tiles, orders l <= 3;
+ * Schedule of tt_fsi_apply on the fast path (12-bit tiles, orders l <= 4;
  * other plans ignore it).  fused = 0 (the default): a tile launch, then a
  * combine launch (the cross-tile sums of Section 3.3); the tracing of
  * tt_fsi_plan_profile splits the time between the two.  fused != 0: one

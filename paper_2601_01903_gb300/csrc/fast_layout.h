@@ -1,4 +1,4 @@
-// Shared-memory layout of the fast tile path (12-bit tiles, orders l <= 3),
+// Shared-memory layout of the fast tile path (12-bit tiles, orders l <= 4),
 // used by the kernels (as compile-time constants) and by the host plan.
 //
 // A tile's 12 low bits form three 4-bit groups A (bits 0-3), B (4-7) and
@@ -45,7 +45,7 @@ TTFSI_HD constexpr int n4_max(int L) {
 // u in [rd + kB, 8]; grouped by kB, then rank(sigma_B), then u
 TTFSI_HD constexpr int off8(int rd, int kB) {
     return (kB > 0 ? (9 - rd) : 0) + (kB > 1 ? 4 * (8 - rd) : 0) + (kB > 2 ? 6 * (7 - rd) : 0) +
-           (kB > 3 ? 4 * (6 - rd) : 0);
+           (kB > 3 ? 4 * (6 - rd) : 0) + (kB > 4 ? (5 - rd) : 0);
 }
 TTFSI_HD constexpr int s8(int L, int rd) { return off8(rd, L - rd + 1); }
 TTFSI_HD constexpr int n8(int L, int rd) { return c4(rd) * s8(L, rd); }
@@ -62,7 +62,7 @@ TTFSI_HD constexpr int nst(int L) {
 // group C), sigma_C grouped by kC = |sigma_C|, then rank, then j
 TTFSI_HD constexpr int offC(int k8, int kC) {
     return (kC > 0 ? (13 - k8) : 0) + (kC > 1 ? 4 * (12 - k8) : 0) + (kC > 2 ? 6 * (11 - k8) : 0) +
-           (kC > 3 ? 4 * (10 - k8) : 0);
+           (kC > 3 ? 4 * (10 - k8) : 0) + (kC > 4 ? (9 - k8) : 0);
 }
 TTFSI_HD constexpr int ch8(int L, int k8) { return offC(k8, L - k8 + 1); }
 // channel blocks ordered by round rd, then kB, then (rank sigma_A, rank sigma_B)

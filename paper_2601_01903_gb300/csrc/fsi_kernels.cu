@@ -25,12 +25,13 @@
 #include <vector>
 
 #include "fast_layout.h"
+#include "fast_tile.cuh"
 #include "fsi_plan.h"
+#include "tile_common.cuh"
 #include "tt_fsi.h"
 
 namespace ttfsi {
 
-enum : int { kErrNonFinite = 1, kErrTimeout = 2 };
 
 struct TileArgs {
     const void *v;
@@ -56,49 +57,6 @@ struct CombineArgs {
     int b, h, n_ch, shift_cap, mob_only;
     long long n_out;
     long long game0;
-};
-
-// ----------------------------------------------------------------------------
-// float64 -> fixed point by integer operations only (GB300's float64 units,
-// conversions included, run at about 2 per clock per SM; its integer ALUs at
-// 64-128).  E is the tile's largest biased exponent, P the headroom:
-// V = round(v * 2^(P + 1022 - E)), half away from zero.
-// ----------------------------------------------------------------------------
-__device__ __forceinline__ long long to_fixed(unsigned long long bits, int E, int P) {
-    int e = (int)((bits >> 52) & 0x7ff);
-    unsigned long long mant = bits & 0x000FFFFFFFFFFFFFull;
-    if (e != 0)
-        mant |= (1ull << 52);
-    else
-        e = 1;
-    int sh = 53 - P + (E - e);
-    unsigned long long r;
-    if (sh <= 0)
-        r = mant;  // P = 53 and e = E: exact
-    else if (sh >= 64)
-        r = 0;
-    else
-        r = ((mant >> (sh - 1)) + 1) >> 1;  // = (mant + 2^(sh-1)) >> sh: round half up
-    long long x = (long long)r;
-    return (bits >> 63) ? -x : x;
-}
-
-template <typename Acc>
-struct TileTraits;
-template <>
-struct TileTraits<long long> {
-    using In = unsigned long long;
-    static constexpr bool exact = true;
-};
-template <>
-struct TileTraits<double> {
-    using In = double;
-    static constexpr bool exact = false;
-};
-template <>
-struct TileTraits<float> {
-    using In = float;
-    static constexpr bool exact = false;
 };
 
 template <typename Acc>
@@ -188,407 +146,6 @@ __global__ void __launch_bounds__(kTileThreads) fsi_tile_kernel(TileArgs a) {
     if constexpr (TileTraits<Acc>::exact) {
         if (tid == 0) a.tile_exp[(game << a.h) + tile] = a.prec_bits + 1022 - E;
     }
-}
-
-// ----------------------------------------------------------------------------
-// Fast tile kernel for b = 12, l <= 3.
-//
-// Moebius: the 16 values a thread holds always differ in 4 tile bits; three
-// register phases (bits 8-11, 4-7, 0-3) with two shared-memory transposes.
-// Shared layout of the tile: element e at e ^ ((e >> 8) & 15), which keeps
-// every half-warp on 16 distinct 8-byte bank pairs in all three phases.
-//
-// Ranked superset sums (the (|S|, |T|) counters of Section 3.3) in three
-// 4-bit groups, ranked by the absolute count u = |T n processed bits| (the
-// layout and its closed-form offsets are in fast_layout.h).  With u fixed,
-// every input of a group step has exactly one rank, so each step is a plain
-// superset sum over 4 bits in registers:
-//   block 1 (group A, registers): Z_A(sigma_A, t) from the Moebius values;
-//   block 2 (group B): item (sigma_A, u) x 16 lanes tau_C gathers the 16
-//     values Z_A(sigma_A, u - |tau_B|; tau_B) and writes Z_AB(sigma_A u
-//     sigma_B, u) for every sigma_B the order allows;
-//   block 3 (group C): item (sigma_8, u') per thread gathers Z_AB(sigma_8,
-//     u' - |tau_C|; tau_C) and writes the channels Z(sigma_8 u sigma_C, u').
-// Each output state is written by exactly one thread.  States are processed
-// in rounds rd = |sigma_A| (a state's round never changes), so only one
-// round's level-4 and level-8 states are held in shared memory at a time.
-// The kernel is instantiated per order l, which makes every offset and
-// every pruning decision a compile-time constant.
-//
-// Weighting: the tile, whose high pattern U_H has u_H = |U_H| set bits, forms
-// one partial score per (S_L, s, i) -- i the size of U_H n S_H that a score
-// S = S_L u S_H of size s would see --
-//   G = (-1)^(r-i) sum_j [omega_s(u_H + r - i, |S_L| + j) + [i = u_H][j = 0]] Y(S_L, j),
-// r = s - |S_L|, so that phi(S) = sum over tiles of G(S_L, s, |U_H n S_H|).
-// On the exact path G is an exact int128 (weights as integer numerators).
-// ----------------------------------------------------------------------------
-struct FastArgs {
-    const void *v;
-    void *G;
-    int *tile_exp;
-    int *err;
-    const int32_t *gtab;
-    const long long *wnum;
-    const long long *wden;
-    const double *wf64;
-    const float *wf32;
-    int n_g;
-    int d, h, ell, prec_bits, load_mask;
-    int g_split31;        // exact weighting by 32 x 32-bit products (see the plan)
-    int prefetch_ahead;   // tile launch: prefetch the tile this many CTAs ahead into L2 (0: off)
-    long long game0;
-};
-
-template <typename Acc>
-struct GTraits {
-    using G = Acc;
-};
-template <>
-struct GTraits<long long> {
-    using G = __int128;
-};
-
-__device__ __forceinline__ double i128_to_double(__int128 x) {
-    const bool neg = x < 0;
-    unsigned __int128 u = neg ? (unsigned __int128)(-x) : (unsigned __int128)x;
-    unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
-    double r = (double)hi * 18446744073709551616.0 + (double)lo;
-    return neg ? -r : r;
-}
-
-// Full 128-bit product of two signed 64-bit integers.
-__device__ __forceinline__ __int128 mul_wide(long long a, long long b) {
-    const unsigned long long lo = (unsigned long long)a * (unsigned long long)b;
-    const long long hi = __mul64hi(a, b);
-    return (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | lo);
-}
-
-__device__ __forceinline__ int tile_phys(int e) { return e ^ ((e >> 8) & 15); }
-
-template <typename Acc>
-__device__ __forceinline__ void mobius16(Acc (&x)[16]) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int r = 0; r < 16; ++r)
-            if (!((r >> q) & 1)) x[r | (1 << q)] -= x[r];
-}
-
-// Superset sums over 4 bits, correct wherever |sigma_r| <= O.  After the
-// level of bit q an entry is still needed only if it has at most O set bits
-// among bits 0..q, so the update of entry r at bit q is skipped unless r has
-// at most O set bits below q.
-template <int O, typename Acc>
-__device__ __forceinline__ void zeta16(Acc (&x)[16]) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int r = 0; r < 16; ++r)
-            if (!((r >> q) & 1) && fast::pc4(r & ((1 << q) - 1)) <= O) x[r] += x[r | (1 << q)];
-}
-
-// Block 1 of round RD: the level-4 states (sigma_A, t), |sigma_A| = RD, of
-// this thread's position (tau_B, tau_C) from its 16 Moebius values.
-template <int L, int RD, typename Acc>
-__device__ __forceinline__ void fast_block1(const Acc (&x)[16], Acc *regB, int pos) {
-#pragma unroll
-    for (int sg = 0; sg < 16; ++sg) {
-        if (fast::pc4(sg) != RD) continue;
-        const int base = fast::rank4(sg) * (5 - RD) - RD;
-#pragma unroll
-        for (int t = RD; t <= 4; ++t) {
-            Acc acc = 0;
-#pragma unroll
-            for (int tau = 0; tau < 16; ++tau)
-                if ((tau & sg) == sg && fast::pc4(tau) == t) acc += x[tau];
-            regB[(base + t) * 256 + pos] = acc;
-        }
-    }
-}
-
-// Block 2 of round RD: items (rank sigma_A, u), u in [RD, 8], 16 lanes over
-// tau_C.  Level-8 states go to regA[tau_C * NST + state].
-template <int L, int RD, typename Acc>
-__device__ __forceinline__ void fast_block2(const Acc *regB, Acc *regA, int tid) {
-    constexpr int O = L - RD;
-    constexpr int NU = 9 - RD;
-    constexpr int NIT = fast::c4(RD) * NU;
-    constexpr int S8 = fast::s8(L, RD);
-    constexpr int NST = fast::nst(L);
-    const int t3 = tid & 15;
-    for (int it = tid >> 4; it < NIT; it += kTileThreads / 16) {
-        const int rA = it / NU, uu = it - rA * NU;  // u = RD + uu
-        // input tau_B: level-4 state (sigma_A, t = u - |tau_B|), t in [RD, 4]
-        const Acc *src = regB + (rA * (5 - RD) + uu) * 256 + t3;
-        Acc x[16];
-#pragma unroll
-        for (int tau = 0; tau < 16; ++tau) {
-            const int pc = fast::pc4(tau);
-            Acc val = 0;
-            if (uu >= pc && uu - pc <= 4 - RD) val = src[16 * tau - 256 * pc];
-            x[tau] = val;
-        }
-        zeta16<O>(x);
-        Acc *dst = regA + t3 * NST + rA * S8 + uu;
-#pragma unroll
-        for (int sb = 0; sb < 16; ++sb) {
-            const int kB = fast::pc4(sb);
-            if (kB > O) continue;
-            // state (sigma_A u sigma_B, u): off8 + rank * (9 - RD - kB) + (u - RD - kB)
-            if (uu >= kB) dst[fast::off8(RD, kB) + fast::rank4(sb) * (9 - RD - kB) - kB] = x[sb];
-        }
-    }
-}
-
-// Block 3 item of round RD, group kB = |sigma_B|: (rank sigma_A, rank
-// sigma_B, u'), u' in [RD + KB, 12]; writes the channels of sigma_8 u sigma_C.
-template <int L, int RD, int KB, typename Acc>
-__device__ __forceinline__ void fast_block3_item(int local, const Acc *regA, Acc *regY) {
-    constexpr int K8 = RD + KB;
-    constexpr int O = L - K8;
-    constexpr int NU = 13 - K8;
-    constexpr int NB = fast::c4(KB);
-    constexpr int S8 = fast::s8(L, RD);
-    constexpr int NST = fast::nst(L);
-    constexpr int OFF8 = fast::off8(RD, KB);
-    constexpr int CG = fast::chan_group(L, RD, KB);
-    constexpr int CH = fast::ch8(L, K8);
-    const int pair = local / NU, uu = local - pair * NU;  // u' = K8 + uu
-    const int rA = pair / NB, rB = pair - rA * NB;
-    // input tau_C: level-8 state (sigma_8, u' - |tau_C|), u' - |tau_C| in [K8, 8]
-    const Acc *src = regA + rA * S8 + OFF8 + rB * (9 - K8) + uu;
-    Acc x[16];
-#pragma unroll
-    for (int tau = 0; tau < 16; ++tau) {
-        const int pc = fast::pc4(tau);
-        Acc val = 0;
-        if (uu >= pc && uu - pc <= 8 - K8) val = src[tau * NST - pc];
-        x[tau] = val;
-    }
-    zeta16<O>(x);
-    Acc *dst = regY + CG + pair * CH + uu;
-#pragma unroll
-    for (int sc = 0; sc < 16; ++sc) {
-        const int kC = fast::pc4(sc);
-        if (kC > O) continue;
-        // channel (sigma_8 u sigma_C, j = u' - K8 - kC)
-        if (uu >= kC) dst[fast::offC(K8, kC) + fast::rank4(sc) * (13 - K8 - kC) - kC] = x[sc];
-    }
-}
-
-// Block 3 of round RD: the groups kB = 0..L-RD one after another, each
-// padded to whole warps so that a warp never mixes two pruning orders.
-template <int L, int RD, typename Acc>
-__device__ __forceinline__ void fast_block3(const Acc *regA, Acc *regY, int tid) {
-    constexpr int M = L - RD;
-    constexpr int P0 = fast::pad32(fast::g3(RD, 0));
-    constexpr int P1 = M >= 1 ? fast::pad32(fast::g3(RD, 1)) : 0;
-    constexpr int P2 = M >= 2 ? fast::pad32(fast::g3(RD, 2)) : 0;
-    constexpr int P3 = M >= 3 ? fast::pad32(fast::g3(RD, 3)) : 0;
-    constexpr int TOTAL = P0 + P1 + P2 + P3;
-    for (int it = tid; it < TOTAL; it += kTileThreads) {
-        if (it < P0) {
-            if (it < fast::g3(RD, 0)) fast_block3_item<L, RD, 0>(it, regA, regY);
-        } else if (it < P0 + P1) {
-            if constexpr (M >= 1) {
-                const int l = it - P0;
-                if (l < fast::g3(RD, 1)) fast_block3_item<L, RD, 1>(l, regA, regY);
-            }
-        } else if (it < P0 + P1 + P2) {
-            if constexpr (M >= 2) {
-                const int l = it - P0 - P1;
-                if (l < fast::g3(RD, 2)) fast_block3_item<L, RD, 2>(l, regA, regY);
-            }
-        } else {
-            if constexpr (M >= 3) {
-                const int l = it - P0 - P1 - P2;
-                if (l < fast::g3(RD, 3)) fast_block3_item<L, RD, 3>(l, regA, regY);
-            }
-        }
-    }
-}
-
-// Round RD: blocks 2 and 3, then block 1 of the next round, which only
-// touches the level-4 region that block 2 has finished reading.
-template <int L, int RD, typename Acc>
-__device__ __forceinline__ void fast_round(const Acc (&x)[16], Acc *regA, Acc *regB, Acc *regY, int tid,
-                                           int pos) {
-    fast_block2<L, RD>(regB, regA, tid);
-    __syncthreads();
-    fast_block3<L, RD>(regA, regY, tid);
-    if constexpr (RD < L) fast_block1<L, RD + 1>(x, regB, pos);
-    __syncthreads();
-    if constexpr (RD < L) fast_round<L, RD + 1>(x, regA, regB, regY, tid, pos);
-}
-
-// One partial score: sum over j < J = 13 - |S_L| of the weight
-// omega_s(p, |S_L| + j) (plus 1 at j = 0 when ident) times the channel
-// Y(S_L, j); wo indexes omega_s(p, |S_L|).  All loads are issued before the
-// products.  Exact path: weights are integer numerators over D_s (the
-// identity term is D_s); with g_split31 every product is two 32 x 32-bit
-// multiply-adds (y = yh 2^31 + yl), else a full 64 x 64 -> 128-bit product.
-template <typename Acc, int J>
-__device__ __forceinline__ typename GTraits<Acc>::G fast_g_entry(const FastArgs &a, const Acc *y, long long wo, int s,
-                                                                bool ident) {
-    using GT = typename GTraits<Acc>::G;
-    Acc yv[J];
-#pragma unroll
-    for (int j = 0; j < J; ++j) yv[j] = y[j];
-    if constexpr (TileTraits<Acc>::exact) {
-        long long c[J];
-#pragma unroll
-        for (int j = 0; j < J; ++j) c[j] = __ldg(a.wnum + wo + j);
-        if (ident) c[0] += __ldg(a.wden + s);
-        if (a.g_split31) {
-            long long acc_h = 0, acc_l = 0;
-#pragma unroll
-            for (int j = 0; j < J; ++j) {
-                acc_h += (long long)(int)c[j] * (int)(yv[j] >> 31);
-                acc_l += (long long)(int)c[j] * (int)(yv[j] & 0x7fffffffll);
-            }
-            return (GT)(((unsigned __int128)(__int128)acc_h) << 31) + (GT)acc_l;
-        }
-        GT acc = 0;
-#pragma unroll
-        for (int j = 0; j < J; ++j) acc += mul_wide(yv[j], c[j]);
-        return acc;
-    } else {
-        Acc acc = 0;
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-            Acc c = (sizeof(Acc) == 4) ? (Acc)__ldg(a.wf32 + wo + j) : (Acc)__ldg(a.wf64 + wo + j);
-            if (j == 0 && ident) c += (Acc)1;
-            acc += yv[j] * c;
-        }
-        return acc;
-    }
-}
-
-template <typename Acc, int L>
-__device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long long game, const long long tile) {
-    using In = typename TileTraits<Acc>::In;
-    using GT = typename GTraits<Acc>::G;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Acc *regA = reinterpret_cast<Acc *>(smem_raw);  // tile, then one round's level-8 states
-    Acc *regB = regA + fast::regA_elems(L);          // one round's level-4 states
-    Acc *regY = regB + fast::regB_elems(L);          // channels
-    __shared__ int s_emax;
-
-    const int tid = threadIdx.x;
-    const In *src = reinterpret_cast<const In *>(a.v) + (game << a.d) + (tile << 12);
-
-    Acc x[16];
-    int E = 0;
-    // ---- load (element tid + 256 r), register bits 8-11 ----
-    if constexpr (TileTraits<Acc>::exact) {
-        In raw[16];
-        int emax = 0;
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            raw[r] = __ldg(src + ((tid + 256 * r) & a.load_mask));
-            emax = max(emax, (int)((raw[r] >> 52) & 0x7ff));
-        }
-        for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-        if (tid == 0) s_emax = 0;
-        __syncthreads();
-        if ((tid & 31) == 0) atomicMax(&s_emax, emax);
-        __syncthreads();
-        E = s_emax;
-        const bool bad = (E == 0x7ff);
-        if (bad && tid == 0) atomicOr(a.err, kErrNonFinite);
-        if (E == 0) E = 1;
-#pragma unroll
-        for (int r = 0; r < 16; ++r) x[r] = bad ? 0ll : to_fixed(raw[r], E, a.prec_bits);
-    } else {
-#pragma unroll
-        for (int r = 0; r < 16; ++r) x[r] = (Acc)__ldg(src + ((tid + 256 * r) & a.load_mask));
-    }
-    mobius16(x);
-#pragma unroll
-    for (int r = 0; r < 16; ++r) regA[tile_phys(tid + 256 * r)] = x[r];
-    __syncthreads();
-    // ---- bits 4-7: e = (tid & 15) | r << 4 | (tid >> 4) << 8 ----
-    {
-        const int e0 = (tid & 15) | ((tid >> 4) << 8);
-#pragma unroll
-        for (int r = 0; r < 16; ++r) x[r] = regA[tile_phys(e0 | (r << 4))];
-        mobius16(x);
-#pragma unroll
-        for (int r = 0; r < 16; ++r) regA[tile_phys(e0 | (r << 4))] = x[r];
-    }
-    __syncthreads();
-    // ---- bits 0-3: t3 = tid & 15 (tau_C, bits 8-11), t2 = tid >> 4 (tau_B, bits 4-7) ----
-    const int t3 = tid & 15, t2 = tid >> 4;
-    {
-        const int e0 = (t2 << 4) | (t3 << 8);
-#pragma unroll
-        for (int r = 0; r < 16; ++r) x[r] = regA[tile_phys(e0 | r)];
-        mobius16(x);
-    }
-    // ---- ranked sums: block 1 of round 0, then the rounds ----
-    const int pos = t3 + 16 * t2;
-    fast_block1<L, 0>(x, regB, pos);
-    __syncthreads();
-    fast_round<L, 0>(x, regA, regB, regY, tid, pos);
-    // ---- partial scores G(S_L, s, i) of this tile ----
-    const int uH = __popcll((unsigned long long)tile);
-    const int P1 = a.h + 1, Q1 = 13;
-    // partial scores of a game are stored entry-major, [n_g][2^h tiles], so
-    // that the combine's lanes (consecutive tiles) read consecutive addresses
-    const long long ntile = 1ll << a.h;
-    GT *gdst = reinterpret_cast<GT *>(a.G) + (game << a.h) * (long long)a.n_g + tile;
-    for (int g = tid; g < a.n_g; g += kTileThreads) {
-        const int cb = __ldg(a.gtab + 2 * g), code = __ldg(a.gtab + 2 * g + 1);
-        const int sL = code & 0xff, s = (code >> 8) & 0xff, i = code >> 16;
-        const int r = s - sL, pp = uH + r - i;
-        GT acc = 0;
-        if (i <= uH && r - i <= a.h - uH) {
-            // entries are sorted by |S_L|, so a warp almost always takes one case
-            const long long wo = ((long long)s * P1 + pp) * Q1 + sL;
-            const bool ident = (i == uH);
-            switch (sL) {
-                case 0: acc = fast_g_entry<Acc, 13>(a, regY + cb, wo, s, ident); break;
-                case 1: acc = fast_g_entry<Acc, 12>(a, regY + cb, wo, s, ident); break;
-                case 2: acc = fast_g_entry<Acc, 11>(a, regY + cb, wo, s, ident); break;
-                default: acc = fast_g_entry<Acc, 10>(a, regY + cb, wo, s, ident); break;
-            }
-            if ((r - i) & 1) acc = -acc;
-        }
-        gdst[g * ntile] = acc;
-    }
-    if constexpr (TileTraits<Acc>::exact) {
-        if (tid == 0) a.tile_exp[(game << a.h) + tile] = a.prec_bits + 1022 - E;
-    }
-}
-
-// One tile of a plan with order a.ell (1..3): the instantiation for that order.
-template <typename Acc>
-__device__ __forceinline__ void tile_fast_dispatch(const FastArgs &a, const long long game, const long long tile) {
-    switch (a.ell) {
-        case 1: tile_fast_body<Acc, 1>(a, game, tile); break;
-        case 2: tile_fast_body<Acc, 2>(a, game, tile); break;
-        default: tile_fast_body<Acc, 3>(a, game, tile); break;
-    }
-}
-
-// One CTA per (tile, game).  CTAs start roughly in linear order, so each asks
-// L2 to prefetch the input of the tile prefetch_ahead CTAs later (about one
-// wave of resident CTAs), which that CTA will then load from L2, not HBM.
-template <typename Acc, int L>
-__global__ void __launch_bounds__(kTileThreads, 2) fsi_tile_fast_kernel(FastArgs a) {
-    using In = typename TileTraits<Acc>::In;
-    if (a.prefetch_ahead > 0) {
-        const long long lin = (long long)blockIdx.y * gridDim.x + blockIdx.x + a.prefetch_ahead;
-        if (lin < (long long)gridDim.x * gridDim.y) {
-            const long long gy = lin / gridDim.x, gx = lin - gy * gridDim.x;
-            const char *base = reinterpret_cast<const char *>(reinterpret_cast<const In *>(a.v) +
-                                                              ((a.game0 + gy) << a.d) + (gx << fast::kBits));
-            const int bytes = (a.load_mask + 1) * (int)sizeof(In);
-            for (int o = threadIdx.x * 128; o < bytes; o += kTileThreads * 128)
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(base + o));
-        }
-    }
-    tile_fast_body<Acc, L>(a, a.game0 + blockIdx.y, blockIdx.x);
 }
 
 // ----------------------------------------------------------------------------
@@ -1037,9 +594,11 @@ cudaError_t allow_max_smem_fast() {
     cudaError_t e = allow_max_smem(fsi_tile_fast_kernel<Acc, 1>);
     if (e == cudaSuccess) e = allow_max_smem(fsi_tile_fast_kernel<Acc, 2>);
     if (e == cudaSuccess) e = allow_max_smem(fsi_tile_fast_kernel<Acc, 3>);
+    if (e == cudaSuccess) e = allow_max_smem(fsi_tile_fast_kernel<Acc, 4>);
     if (e == cudaSuccess) e = allow_max_smem(fsi_apply_fast_kernel<Acc, 1>);
     if (e == cudaSuccess) e = allow_max_smem(fsi_apply_fast_kernel<Acc, 2>);
     if (e == cudaSuccess) e = allow_max_smem(fsi_apply_fast_kernel<Acc, 3>);
+    if (e == cudaSuccess) e = allow_max_smem(fsi_apply_fast_kernel<Acc, 4>);
     return e;
 }
 
@@ -1053,7 +612,8 @@ cudaError_t fused_grid(const Plan &p, int *grid) {
     switch (p.ell) {
         case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fsi_apply_fast_kernel<Acc, 1>, kTileThreads, p.smem_fast); break;
         case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fsi_apply_fast_kernel<Acc, 2>, kTileThreads, p.smem_fast); break;
-        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fsi_apply_fast_kernel<Acc, 3>, kTileThreads, p.smem_fast); break;
+        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fsi_apply_fast_kernel<Acc, 3>, kTileThreads, p.smem_fast); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fsi_apply_fast_kernel<Acc, 4>, kTileThreads, p.smem_fast); break;
     }
     *grid = std::max(1, occ) * sms;
     return e;
@@ -1129,7 +689,8 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
         switch (p.ell) {
             case 1: fsi_apply_fast_kernel<Acc, 1><<<grid, kTileThreads, p.smem_fast, st>>>(aa); break;
             case 2: fsi_apply_fast_kernel<Acc, 2><<<grid, kTileThreads, p.smem_fast, st>>>(aa); break;
-            default: fsi_apply_fast_kernel<Acc, 3><<<grid, kTileThreads, p.smem_fast, st>>>(aa); break;
+            case 3: fsi_apply_fast_kernel<Acc, 3><<<grid, kTileThreads, p.smem_fast, st>>>(aa); break;
+            default: fsi_apply_fast_kernel<Acc, 4><<<grid, kTileThreads, p.smem_fast, st>>>(aa); break;
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_status(e);
@@ -1155,7 +716,8 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
             switch (p.ell) {
                 case 1: fsi_tile_fast_kernel<Acc, 1><<<g1, kTileThreads, p.smem_fast, st>>>(fa); break;
                 case 2: fsi_tile_fast_kernel<Acc, 2><<<g1, kTileThreads, p.smem_fast, st>>>(fa); break;
-                default: fsi_tile_fast_kernel<Acc, 3><<<g1, kTileThreads, p.smem_fast, st>>>(fa); break;
+                case 3: fsi_tile_fast_kernel<Acc, 3><<<g1, kTileThreads, p.smem_fast, st>>>(fa); break;
+                default: fsi_tile_fast_kernel<Acc, 4><<<g1, kTileThreads, p.smem_fast, st>>>(fa); break;
             }
         } else {
             fsi_tile_kernel<Acc><<<g1, kTileThreads, p.smem_tile, st>>>(ta);

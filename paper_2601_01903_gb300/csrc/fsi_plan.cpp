@@ -143,14 +143,14 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
     const size_t elem = (arith == TT_FSI_ARITH_F32) ? 4 : 8;
     const size_t smem_budget = 224 * 1024;  // 227 KB opt-in per CTA, minus static
 
-    // Tile width.  Orders l <= 3 (below d) take the fast path, whose tile is
+    // Tile width.  Orders l <= 4 (below d) take the fast path, whose tile is
     // always 12 bits: a game with d < 12 is processed as the 12-player game
     // with 12 - d null players appended (v_ext(S) = v(S n [d])); its
     // Moebius coefficients vanish on every T that contains a null player and
     // Eq. correction's weights depend only on |S| and |T|, so the scores of
     // the sets inside [d] are unchanged.  Otherwise: the largest b <=
     // min(d, 12) whose two ranked-sum buffers fit in shared memory.
-    const bool want_fast = !p.mob_only && ell <= 3;
+    const bool want_fast = !p.mob_only && ell <= 4;
     int b = want_fast ? kMaxTileBits : std::min(d, kMaxTileBits);
     for (;; --b) {
         if (want_fast) {
@@ -287,7 +287,7 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
             p.tasks[i * 4 + 3] = g_of.at({SL, popc64(S)});
         }
         p.fast12 = p.smem_fast <= smem_budget;
-        if (!p.fast12) return TT_FSI_ERR_UNSUPPORTED;  // does not happen for l <= 3
+        if (!p.fast12) return TT_FSI_ERR_UNSUPPORTED;  // does not happen for l <= 4
     }
 
     // ---------------- combined weights omega_s(p, q) ----------------------

@@ -50,7 +50,7 @@ struct Plan {
     std::vector<int32_t> trans;   // 2 entries per (level, output state)
     int buf_elems = 0;            // elements of one ping-pong buffer
 
-    // Fast tile path (b = 12, l <= 3): Moebius in registers, ranked sums in
+    // Fast tile path (b = 12, l <= 4): Moebius in registers, ranked sums in
     // three 4-bit groups by absolute rank, run in rounds r = |sigma n bits
     // 0..3|; every offset is a closed form (fast_layout.h), so the only table
     // is gtab.  Shared memory: regA (tile, then one round's level-8 states),

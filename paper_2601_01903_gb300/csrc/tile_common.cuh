@@ -1,0 +1,56 @@
+// Device helpers shared by the tile kernels: the fault bits, the exact
+// float64 -> fixed-point conversion and the per-arithmetic traits.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fsi_plan.h"
+
+namespace ttfsi {
+
+enum : int { kErrNonFinite = 1, kErrTimeout = 2 };
+
+// ----------------------------------------------------------------------------
+// float64 -> fixed point by integer operations only (GB300's float64 units,
+// conversions included, run at about 2 per clock per SM; its integer ALUs at
+// 64-128).  E is the tile's largest biased exponent, P the headroom:
+// V = round(v * 2^(P + 1022 - E)), half away from zero.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ long long to_fixed(unsigned long long bits, int E, int P) {
+    int e = (int)((bits >> 52) & 0x7ff);
+    unsigned long long mant = bits & 0x000FFFFFFFFFFFFFull;
+    if (e != 0)
+        mant |= (1ull << 52);
+    else
+        e = 1;
+    int sh = 53 - P + (E - e);
+    unsigned long long r;
+    if (sh <= 0)
+        r = mant;  // P = 53 and e = E: exact
+    else if (sh >= 64)
+        r = 0;
+    else
+        r = ((mant >> (sh - 1)) + 1) >> 1;  // = (mant + 2^(sh-1)) >> sh: round half up
+    long long x = (long long)r;
+    return (bits >> 63) ? -x : x;
+}
+
+template <typename Acc>
+struct TileTraits;
+template <>
+struct TileTraits<long long> {
+    using In = unsigned long long;
+    static constexpr bool exact = true;
+};
+template <>
+struct TileTraits<double> {
+    using In = double;
+    static constexpr bool exact = false;
+};
+template <>
+struct TileTraits<float> {
+    using In = float;
+    static constexpr bool exact = false;
+};
+
+}  // namespace ttfsi

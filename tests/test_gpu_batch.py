@@ -56,7 +56,7 @@ def test_uneven_batch_all_paths_match_oracle(oracle_mod):
 
 def test_mixed_batch_with_games_off_the_fast_path(oracle_mod):
     games, vs, off, poff = [], [], 0, 0
-    specs = [(12, 3), (5, 5), (9, 4), (14, 2), (3, 1), (13, 13), (16, 1)]
+    specs = [(12, 3), (5, 5), (9, 4), (14, 2), (3, 1), (13, 13), (16, 1), (11, 5), (15, 4)]
     for i, (d, ell) in enumerate(specs):
         v = synthetic.Stream(300 + i, d).normal(1 << d)
         games.append((d, ell, off, poff))

@@ -222,3 +222,21 @@ def test_fused_wait_timeout_is_reported_and_recoverable():
     again = plan.apply(v)
     plan.check()
     assert torch.equal(again, ref)
+
+
+@pytest.mark.parametrize("arith", ["exact", "f64"])
+@pytest.mark.parametrize("d,B", [(16, 2), (14, 3), (7, 4), (5, 2)])
+def test_order_4_fast_path(oracle_mod, arith, d, B):
+    """Order 4 on the 12-bit-tile path: several tiles (d = 14, 16) and
+    games smaller than a tile (d = 5, 7: null players fill the tile)."""
+    v = _noise_games(d, B, seed=400 + d, v0=False)
+    got, plan = _run(v, d, 4, arith)
+    assert plan.tile_bits == 12
+    assert _rel_err(got, oracle_mod.fsi(v, d, 4), v) <= TOL
+
+
+def test_order_4_float32_error_is_small(oracle_mod):
+    d = 15
+    v = _noise_games(d, 2, seed=77)
+    got, _ = _run(v, d, 4, "f32")
+    assert _rel_err(got, oracle_mod.fsi(v, d, 4), v) <= 1e-4
