@@ -71,6 +71,27 @@ typedef enum {
     TT_FSI_ARITH_F32 = 2
 } tt_fsi_arith;
 
+/*
+ * Interaction index a plan computes.  Every one is a sum over the supersets
+ * T of S of a weight W(|S|, |T|) times the Moebius coefficient a(T), so all
+ * run on the same kernels with different weight tables:
+ *  TT_FSI_INDEX_FSI   Faithful Shapley interactions of order l (Eq.
+ *                     fsi_closed with Eq. correction and Eq. weight).
+ *  TT_FSI_INDEX_SII   Shapley interaction index (Appendix A, discrete-
+ *                     derivative form); W = 1 / (|T| - |S| + 1).
+ *  TT_FSI_INDEX_BII   Banzhaf interaction index (Appendix A: uniform
+ *                     weights); W = 2^-(|T| - |S|).
+ *  TT_FSI_INDEX_STII  Shapley-Taylor index of order l (Appendix A):
+ *                     a(S) for |S| < l; W = 1 / C(|T|, l) for |S| = l.
+ * SII and BII do not depend on l; l only bounds the scored sets |S| <= l.
+ */
+typedef enum {
+    TT_FSI_INDEX_FSI = 0,
+    TT_FSI_INDEX_SII = 1,
+    TT_FSI_INDEX_BII = 2,
+    TT_FSI_INDEX_STII = 3
+} tt_fsi_index;
+
 /* Opaque plan: everything that depends only on (d, l, arithmetic) --
  * weight tables, tile schedule, state-transition tables -- plus device
  * scratch for up to max_batch games.  Immutable after creation; one plan may
@@ -91,6 +112,13 @@ tt_fsi_status tt_fsi_score_masks(int d, int ell, uint64_t *masks_host);
  * success *out holds the plan. */
 tt_fsi_status tt_fsi_plan_create(int d, int ell, tt_fsi_arith arith, int64_t max_batch,
                                  tt_fsi_plan *out);
+
+/* As tt_fsi_plan_create, for any index of tt_fsi_index (tt_fsi_plan_create
+ * is this call with TT_FSI_INDEX_FSI).  TT_FSI_ERR_UNSUPPORTED if the exact
+ * arithmetic cannot hold the index's weights for this d (their common
+ * denominator above 2^60, as for STII at large d); float64 then works. */
+tt_fsi_status tt_fsi_plan_create_index(int d, int ell, tt_fsi_index index, tt_fsi_arith arith,
+                                       int64_t max_batch, tt_fsi_plan *out);
 
 /* Releases a plan and its device memory (synchronizes the device first).
  * Accepts NULL. */
@@ -153,6 +181,9 @@ typedef struct tt_fsi_batch_s *tt_fsi_batch;
  * of a batch (synchronous).  1 <= d <= 30, l >= 1 per game. */
 tt_fsi_status tt_fsi_batch_create(const tt_fsi_game *games_host, int64_t n_games, tt_fsi_arith arith,
                                   tt_fsi_batch *out);
+/* As tt_fsi_batch_create, every game scored with the given index. */
+tt_fsi_status tt_fsi_batch_create_index(const tt_fsi_game *games_host, int64_t n_games, tt_fsi_arith arith,
+                                        tt_fsi_index index, tt_fsi_batch *out);
 void tt_fsi_batch_destroy(tt_fsi_batch batch);
 
 /*

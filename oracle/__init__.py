@@ -21,6 +21,8 @@ What is here:
   against the closed form); d <= 10.
 * ``shapley_permutations`` -- Shapley values (Section 2.1 equation) by
   enumerating every player order; d <= 8.
+* ``interaction`` -- the other indices of Appendix A (SII, Banzhaf BII,
+  Shapley-Taylor STII) by their definitions over discrete derivatives (C).
 * ``masked_game`` -- the model value function with absent features set to a
   baseline, one forward pass per coalition (C).
 * ``mpo_sweep`` -- the paper's own route (Section 3.3 MPO with Algorithm 1's
@@ -92,6 +94,8 @@ def _load():
             lib.oracle_masked_game.argtypes = [i, i, i, p, p, p, p, p, d, p, p, i64, p, p]
             lib.oracle_num_threads.restype = i
             lib.oracle_num_threads.argtypes = []
+            lib.oracle_index_definition.restype = i
+            lib.oracle_index_definition.argtypes = [i, i, i, i64, p, p]
             _lib = lib
     return _lib
 
@@ -211,6 +215,26 @@ def fsi_from_mobius(a, d: int, ell: int) -> np.ndarray:
     m = score_masks(d, ell)
     out = np.empty(m.shape[0], dtype=np.float64)
     _load().oracle_fsi_from_mobius(d, ell, _ptr(a), m.shape[0], _ptr(m), _ptr(out))
+    return out
+
+
+INDEX_CODES = {"sii": 1, "bii": 2, "stii": 3}
+
+
+def interaction(v, d: int, ell: int, index: str) -> np.ndarray:
+    """Scores [B, n_scores] of the interaction index ``index`` ("fsi",
+    "sii", "bii" or "stii") of games v [B, 2^d].  FSI by its closed form
+    (``fsi``); the others by their definitions of Appendix A over discrete
+    derivatives (C, O(n_scores 2^d) per game, d <= 16 in practice)."""
+    if index == "fsi":
+        return fsi(v, d, ell)
+    if ell < 1:
+        raise ValueError("interaction order must be >= 1")
+    v = _as_games(v, d)
+    out = np.empty((v.shape[0], n_scores(d, ell)), dtype=np.float64)
+    rc = _load().oracle_index_definition(d, ell, INDEX_CODES[index], v.shape[0], _ptr(v), _ptr(out))
+    if rc != 0:
+        raise RuntimeError("oracle_index_definition failed")
     return out
 
 

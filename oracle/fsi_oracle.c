@@ -201,6 +201,82 @@ int oracle_fsi(int d, int ell, int64_t B, const double *v, double *phi)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Other interaction indices (Appendix A), by their definitions               */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Discrete derivative of Appendix A: Delta_S v(T) = sum over R subset of S of
+ * (-1)^(|S|-|R|) v(T u R), for T disjoint from S.
+ */
+static double discrete_derivative(const double *v, uint64_t S, int s, uint64_t T)
+{
+    double acc = 0.0;
+    uint64_t R = S;
+    for (;;) {
+        double x = v[T | R];
+        acc += ((s - popcount64(R)) % 2 == 0) ? x : -x;
+        if (R == 0) break;
+        R = (R - 1) & S;
+    }
+    return acc;
+}
+
+/*
+ * Scores of B games by the definitions over discrete derivatives, summing
+ * over every T in the complement of S (ascending submasks, T = {} first):
+ *   index 1, SII (Appendix A, Shapley interaction index):
+ *     sum_T |T|! (d-|S|-|T|)! / (d-|S|+1)! Delta_S v(T)
+ *       = sum_T Delta_S v(T) / ((d-|S|+1) C(d-|S|, |T|));
+ *   index 2, BII (Appendix A, Banzhaf: the uniform weight over the 2^(d-|S|)
+ *     sets T): sum_T 2^-(d-|S|) Delta_S v(T);
+ *   index 3, STII of order l (Appendix A; Sundararajan et al.'s definition):
+ *     Delta_S v({}) for |S| < l, and (l/d) sum_T Delta_S v(T) / C(d-1, |T|)
+ *     for |S| = l.
+ * Work O(n_scores 2^d); meant for d <= 16.  Returns 0, or -1 on bad input.
+ */
+int oracle_index_definition(int d, int ell, int index, int64_t B, const double *v, double *phi)
+{
+    if (d < 1 || d > 24 || ell < 1 || B < 0 || index < 1 || index > 3) return -1;
+    uint64_t n = (uint64_t)1 << d;
+    uint64_t full = n - 1;
+    int64_t n_out = oracle_num_scores(d, ell);
+    uint64_t *masks = (uint64_t *)malloc((size_t)n_out * sizeof(uint64_t));
+    if (!masks) return -1;
+    oracle_score_masks(d, ell, masks);
+    for (int64_t b = 0; b < B; ++b) {
+        const double *vb = v + (size_t)b * n;
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t k = 0; k < n_out; ++k) {
+            uint64_t S = masks[k];
+            int s = popcount64(S);
+            double out = 0.0;
+            if (index == 3 && s < ell) {
+                out = discrete_derivative(vb, S, s, 0);
+            } else {
+                uint64_t comp = full & ~S;
+                uint64_t T = 0;
+                for (;;) {
+                    int t = popcount64(T);
+                    double w;
+                    if (index == 1)
+                        w = 1.0 / ((double)(d - s + 1) * (double)binom_exact(d - s, t));
+                    else if (index == 2)
+                        w = ldexp(1.0, -(d - s));
+                    else
+                        w = ((double)ell / (double)d) / (double)binom_exact(d - 1, t);
+                    out += w * discrete_derivative(vb, S, s, T);
+                    T = (T - comp) & comp; /* next submask of the complement, ascending */
+                    if (T == 0) break;
+                }
+            }
+            phi[(size_t)b * n_out + k] = out;
+        }
+    }
+    free(masks);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Masked-model value function                                              */
 /* ------------------------------------------------------------------------ */
 

@@ -14,6 +14,8 @@ import numpy as np
 from . import native
 
 ARITH = {"exact": 0, "f64": 1, "f32": 2}
+# interaction indices (tt_fsi_index)
+INDEX = {"fsi": 0, "sii": 1, "bii": 2, "stii": 3}
 STATUS = {
     0: "ok", 1: "invalid argument", 2: "unsupported", 3: "out of memory", 4: "CUDA error",
     5: "device wait timed out", 6: "non-finite input", 7: "self-check failed",
@@ -56,12 +58,12 @@ class Plan:
     """tt_fsi_plan(d, l): tables and scratch for FSI of order ``ell`` on
     ``d``-player games, for batches of up to ``max_batch`` games."""
 
-    def __init__(self, d: int, ell: int, arith: str = "exact", max_batch: int = 1):
+    def __init__(self, d: int, ell: int, arith: str = "exact", max_batch: int = 1, index: str = "fsi"):
         self._lib = native.load()
-        self.d, self.ell, self.arith, self.max_batch = d, ell, arith, max_batch
+        self.d, self.ell, self.arith, self.max_batch, self.index = d, ell, arith, max_batch, index
         h = ctypes.c_void_p()
-        _check(self._lib.tt_fsi_plan_create(d, ell, ARITH[arith], max_batch, ctypes.byref(h)),
-               "tt_fsi_plan_create")
+        _check(self._lib.tt_fsi_plan_create_index(d, ell, INDEX[index], ARITH[arith], max_batch,
+                                                  ctypes.byref(h)), "tt_fsi_plan_create_index")
         self._h = h
         self.n_scores = num_scores(d, ell)
 
@@ -122,10 +124,11 @@ class Plan:
                "tt_fsi_plan_set_wait_limit")
 
 
-def fsi(v, d: int, ell: int, arith: str = "exact"):
-    """One-shot FSI of v [B, 2^d] (CUDA tensor)."""
+def fsi(v, d: int, ell: int, arith: str = "exact", index: str = "fsi"):
+    """One-shot interaction scores (FSI by default; index "sii", "bii" or
+    "stii" for the other indices) of v [B, 2^d] (CUDA tensor)."""
     B = 1 if v.dim() == 1 else v.shape[0]
-    p = Plan(d, ell, arith, max_batch=max(1, B))
+    p = Plan(d, ell, arith, max_batch=max(1, B), index=index)
     try:
         out = p.apply(v)
         p.check()
@@ -207,20 +210,21 @@ class Batch:
     is a sequence of (d, ell, v_offset, phi_offset), offsets in elements of
     the batch's packed value and score buffers."""
 
-    def __init__(self, games, arith: str = "exact"):
+    def __init__(self, games, arith: str = "exact", index: str = "fsi"):
         self._lib = native.load()
-        self.arith = arith
+        self.arith, self.index = arith, index
         arr = (_Game * len(games))(*[_Game(int(d), int(l), int(vo), int(po)) for d, l, vo, po in games])
         h = ctypes.c_void_p()
-        _check(self._lib.tt_fsi_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(games), ARITH[arith],
-                                             ctypes.byref(h)), "tt_fsi_batch_create")
+        _check(self._lib.tt_fsi_batch_create_index(ctypes.cast(arr, ctypes.c_void_p), len(games),
+                                                   ARITH[arith], INDEX[index], ctypes.byref(h)),
+               "tt_fsi_batch_create_index")
         self._h = h
         self.n_games = len(games)
 
     @classmethod
-    def from_ragged(cls, g, arith: str = "exact"):
+    def from_ragged(cls, g, arith: str = "exact", index: str = "fsi"):
         return cls([(int(g.d[k]), int(g.ell[k]), int(g.v_off[k]), int(g.phi_off[k]))
-                    for k in range(len(g.d))], arith)
+                    for k in range(len(g.d))], arith, index)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -567,7 +567,7 @@ FastArgs fast_args(const Plan &p) {
     fa.n_g = p.n_g;
     fa.d = p.d;
     fa.h = p.h;
-    fa.ell = p.ell;
+    fa.ell = p.ell_eff;
     fa.prec_bits = p.prec_bits;
     fa.load_mask = (1 << p.load_bits) - 1;
     fa.g_split31 = p.g_split31 ? 1 : 0;
@@ -609,7 +609,7 @@ cudaError_t fused_grid(const Plan &p, int *grid) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    switch (p.ell) {
+    switch (p.ell_eff) {
         case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fsi_apply_fast_kernel<Acc, 1>, kTileThreads, p.smem_fast); break;
         case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fsi_apply_fast_kernel<Acc, 2>, kTileThreads, p.smem_fast); break;
         case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fsi_apply_fast_kernel<Acc, 3>, kTileThreads, p.smem_fast); break;
@@ -686,7 +686,7 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
         if (ev0) cudaEventRecord(ev0, st);
         cudaError_t e = cudaMemsetAsync(p.d_counters, 0, (size_t)(B + 1) * sizeof(int), st);
         if (e != cudaSuccess) return cuda_status(e);
-        switch (p.ell) {
+        switch (p.ell_eff) {
             case 1: fsi_apply_fast_kernel<Acc, 1><<<grid, kTileThreads, p.smem_fast, st>>>(aa); break;
             case 2: fsi_apply_fast_kernel<Acc, 2><<<grid, kTileThreads, p.smem_fast, st>>>(aa); break;
             case 3: fsi_apply_fast_kernel<Acc, 3><<<grid, kTileThreads, p.smem_fast, st>>>(aa); break;
@@ -713,7 +713,7 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
             fa.err = p.d_err;
             fa.game0 = g0;
             fa.prefetch_ahead = p.apply_grid;
-            switch (p.ell) {
+            switch (p.ell_eff) {
                 case 1: fsi_tile_fast_kernel<Acc, 1><<<g1, kTileThreads, p.smem_fast, st>>>(fa); break;
                 case 2: fsi_tile_fast_kernel<Acc, 2><<<g1, kTileThreads, p.smem_fast, st>>>(fa); break;
                 case 3: fsi_tile_fast_kernel<Acc, 3><<<g1, kTileThreads, p.smem_fast, st>>>(fa); break;
@@ -791,12 +791,17 @@ tt_fsi_status tt_fsi_score_masks(int d, int ell, uint64_t *masks_host) {
 
 tt_fsi_status tt_fsi_plan_create(int d, int ell, tt_fsi_arith arith, int64_t max_batch,
                                  tt_fsi_plan *out) {
+    return tt_fsi_plan_create_index(d, ell, TT_FSI_INDEX_FSI, arith, max_batch, out);
+}
+
+tt_fsi_status tt_fsi_plan_create_index(int d, int ell, tt_fsi_index index, tt_fsi_arith arith,
+                                       int64_t max_batch, tt_fsi_plan *out) {
     if (!out) return TT_FSI_ERR_INVALID_ARG;
     *out = nullptr;
     tt_fsi_plan_s *h = new (std::nothrow) tt_fsi_plan_s();
     if (!h) return TT_FSI_ERR_NO_MEMORY;
     Plan &p = h->p;
-    tt_fsi_status st = plan_build_host(p, d, ell, arith, max_batch);
+    tt_fsi_status st = plan_build_host(p, d, ell, arith, max_batch, index);
     if (st != TT_FSI_OK) {
         delete h;
         return st;
@@ -1344,6 +1349,11 @@ extern "C" {
 
 tt_fsi_status tt_fsi_batch_create(const tt_fsi_game *games_host, int64_t n_games, tt_fsi_arith arith,
                                   tt_fsi_batch *out) {
+    return tt_fsi_batch_create_index(games_host, n_games, arith, TT_FSI_INDEX_FSI, out);
+}
+
+tt_fsi_status tt_fsi_batch_create_index(const tt_fsi_game *games_host, int64_t n_games, tt_fsi_arith arith,
+                                        tt_fsi_index index, tt_fsi_batch *out) {
     using namespace ttfsi;
     if (!out || n_games < 0 || (n_games > 0 && !games_host)) return TT_FSI_ERR_INVALID_ARG;
     if (arith != TT_FSI_ARITH_EXACT && arith != TT_FSI_ARITH_F64 && arith != TT_FSI_ARITH_F32)
@@ -1365,7 +1375,7 @@ tt_fsi_status tt_fsi_batch_create(const tt_fsi_game *games_host, int64_t n_games
         auto it = plan_idx.find(key);
         if (it == plan_idx.end()) {
             tt_fsi_plan p = nullptr;
-            st = tt_fsi_plan_create(gm.d, gm.ell, arith, 1, &p);
+            st = tt_fsi_plan_create_index(gm.d, gm.ell, index, arith, 1, &p);
             if (st != TT_FSI_OK) break;
             it = plan_idx.emplace(key, (int)b->plans.size()).first;
             b->plans.push_back(p);

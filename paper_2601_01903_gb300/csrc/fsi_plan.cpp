@@ -105,6 +105,21 @@ Rational weight_rational(int ell, int s, int t) {
     return r;
 }
 
+Rational index_weight(tt_fsi_index index, int ell, int s, int t) {
+    if (t <= s || s < 0) return Rational{};
+    switch (index) {
+        case TT_FSI_INDEX_FSI: return weight_rational(ell, s, t);
+        case TT_FSI_INDEX_SII: return rat_make(1, (__int128)(t - s + 1));
+        case TT_FSI_INDEX_BII: return rat_make(1, (__int128)1 << (t - s));
+        case TT_FSI_INDEX_STII: {
+            if (s != ell) return Rational{};
+            const Pascal &C = pascal();
+            return rat_make(1, C(t, ell));
+        }
+    }
+    return Rational{};
+}
+
 int64_t num_scores(int d, int ell) {
     if (d < 1 || d > 62 || ell < 1) return -1;
     const Pascal &C = pascal();
@@ -128,17 +143,25 @@ void score_masks(int d, int ell, uint64_t *out) {
     for (int k = 0; k <= std::min(ell, d); ++k) emit_grade(d, k, 0, 0, out, pos);
 }
 
-tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64_t max_batch) {
+tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64_t max_batch,
+                              tt_fsi_index index) {
     if (d < 1 || ell < 1 || max_batch < 1) return TT_FSI_ERR_INVALID_ARG;
+    if (index != TT_FSI_INDEX_FSI && index != TT_FSI_INDEX_SII && index != TT_FSI_INDEX_BII &&
+        index != TT_FSI_INDEX_STII)
+        return TT_FSI_ERR_INVALID_ARG;
     if (arith != TT_FSI_ARITH_EXACT && arith != TT_FSI_ARITH_F64 && arith != TT_FSI_ARITH_F32)
         return TT_FSI_ERR_INVALID_ARG;
     if (d > 30) return TT_FSI_ERR_UNSUPPORTED;
     p.d = d;
     p.ell = ell;
     p.ell_eff = std::min(ell, d);
+    p.index = index;
     p.arith = arith;
     p.max_batch = max_batch;
-    p.mob_only = ell >= d;
+    // With l >= d, FSI and STII leave every Moebius coefficient in place
+    // (no superset has more than d >= l players); SII and BII still sum
+    // over supersets.
+    p.mob_only = ell >= d && (index == TT_FSI_INDEX_FSI || index == TT_FSI_INDEX_STII);
     p.n_out = num_scores(d, ell);
     const size_t elem = (arith == TT_FSI_ARITH_F32) ? 4 : 8;
     const size_t smem_budget = 224 * 1024;  // 227 KB opt-in per CTA, minus static
@@ -150,7 +173,7 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
     // Eq. correction's weights depend only on |S| and |T|, so the scores of
     // the sets inside [d] are unchanged.  Otherwise: the largest b <=
     // min(d, 12) whose two ranked-sum buffers fit in shared memory.
-    const bool want_fast = !p.mob_only && ell <= 4;
+    const bool want_fast = !p.mob_only && p.ell_eff <= 4;
     int b = want_fast ? kMaxTileBits : std::min(d, kMaxTileBits);
     for (;; --b) {
         if (want_fast) {
@@ -163,7 +186,7 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
         if (!p.mob_only) {
             for (int k = 0; k <= b; ++k) {
                 int64_t nk = 0;
-                for (int s = 0; s <= std::min(k, ell); ++s) nk += (int64_t)C(k, s) * (k - s + 1);
+                for (int s = 0; s <= std::min(k, p.ell_eff); ++s) nk += (int64_t)C(k, s) * (k - s + 1);
                 peak = std::max(peak, nk << (b - k));
             }
         }
@@ -191,7 +214,7 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
             for (auto &st : cur) {
                 int s = popc64(st.first);
                 for (int j = 0; j <= k + 1 - s; ++j) nxt.push_back({st.first, j});
-                if (s + 1 <= ell)
+                if (s + 1 <= p.ell_eff)
                     for (int j = 0; j <= k - s; ++j) nxt.push_back({st.first | (1u << k), j});
             }
             std::sort(nxt.begin(), nxt.end());
@@ -227,9 +250,9 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
 
     // fast tile path: shared-memory regions of fast_layout.h
     if (want_fast) {
-        if (fast::n_chan(ell) != p.n_ch) return TT_FSI_ERR_UNSUPPORTED;  // layouts disagree
-        p.fast_regA = fast::regA_elems(ell);
-        p.fast_regB = fast::regB_elems(ell);
+        if (fast::n_chan(p.ell_eff) != p.n_ch) return TT_FSI_ERR_UNSUPPORTED;  // layouts disagree
+        p.fast_regA = fast::regA_elems(p.ell_eff);
+        p.fast_regB = fast::regB_elems(p.ell_eff);
         p.smem_fast = (size_t)(p.fast_regA + p.fast_regB + p.n_ch) * elem;
         p.fast12 = p.smem_fast <= smem_budget;
     }
@@ -238,7 +261,7 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
     std::map<uint32_t, int> ch_base;
     if (p.fast12) {
         for (auto &st : cur)
-            if (st.second == 0) ch_base[st.first] = fast::channel_base(ell, (int)st.first);
+            if (st.second == 0) ch_base[st.first] = fast::channel_base(p.ell_eff, (int)st.first);
     } else if (!p.mob_only) {
         for (size_t i = 0; i < cur.size(); ++i)
             if (cur[i].second == 0) ch_base[cur[i].first] = (int)i;
@@ -269,8 +292,8 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
         std::sort(lows.begin(), lows.end());
         std::map<std::pair<uint32_t, int>, int> g_of;
         p.gtab.clear();
-        for (int sL = 0; sL <= ell; ++sL)
-            for (int sv = sL; sv <= ell; ++sv)
+        for (int sL = 0; sL <= p.ell_eff; ++sL)
+            for (int sv = sL; sv <= p.ell_eff; ++sv)
                 for (auto &lw : lows) {
                     const uint32_t SL = lw.second;
                     if (popc64(SL) != sL || sv > sL + p.h) continue;
@@ -298,9 +321,9 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
         for (int pp = 0; pp < P1; ++pp)
             for (int q = 0; q < Q1; ++q) {
                 Rational acc;
-                if (!p.mob_only && s >= 1) {
+                if (!p.mob_only) {
                     for (int n = 0; n <= p.h - pp; ++n) {
-                        Rational wv = weight_rational(ell, s, pp + q + n);
+                        Rational wv = index_weight(index, ell, s, pp + q + n);
                         if (wv.num == 0) continue;
                         Rational term = rat_mul(wv, rat_make(C(p.h - pp, n), 1));
                         if (n & 1) term.num = -term.num;

@@ -31,13 +31,19 @@ Rational rat_mul(const Rational &a, const Rational &b);
 // s = 0, s > l or t <= l (where C(t-1, l) vanishes).
 Rational weight_rational(int ell, int s, int t);
 
+// Weight W(s, t), t > s, of an interaction index on the Moebius coefficient
+// of a superset T of S (|S| = s, |T| = t); the T = S term is always 1 and is
+// applied separately.
+Rational index_weight(tt_fsi_index index, int ell, int s, int t);
+
 struct Plan {
     int d = 0, ell = 0, ell_eff = 0;
+    tt_fsi_index index = TT_FSI_INDEX_FSI;
     tt_fsi_arith arith = TT_FSI_ARITH_EXACT;
     int64_t max_batch = 0;
     int b = 0, h = 0;         // tile bits, high bits (d = b + h, or d < b = 12 on the fast path)
     int load_bits = 0;        // bits of a tile present in v (min(d, b)); the rest are null players
-    bool mob_only = false;    // l >= d: scores are the Moebius coefficients
+    bool mob_only = false;    // FSI or STII with l >= d: scores are the Moebius coefficients
     int64_t n_out = 0;        // scores per game
     int n_ch = 0;             // channels per tile (states at the last level)
     int prec_bits = 0;        // fixed-point headroom P of the exact path
@@ -99,7 +105,8 @@ struct Plan {
 };
 
 // Builds every host table of the plan (no CUDA calls).  Returns a status.
-tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64_t max_batch);
+tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64_t max_batch,
+                              tt_fsi_index index = TT_FSI_INDEX_FSI);
 
 // Scores and their order.
 int64_t num_scores(int d, int ell);

@@ -110,6 +110,10 @@ def _declare(lib):
     lib.tt_fsi_score_masks.argtypes = [i, i, vp]
     lib.tt_fsi_plan_create.restype = i
     lib.tt_fsi_plan_create.argtypes = [i, i, i, i64, c.POINTER(vp)]
+    lib.tt_fsi_plan_create_index.restype = i
+    lib.tt_fsi_plan_create_index.argtypes = [i, i, i, i, i64, c.POINTER(vp)]
+    lib.tt_fsi_batch_create_index.restype = i
+    lib.tt_fsi_batch_create_index.argtypes = [vp, i64, i, i, c.POINTER(vp)]
     lib.tt_fsi_plan_destroy.restype = None
     lib.tt_fsi_plan_destroy.argtypes = [vp]
     lib.tt_fsi_plan_scratch_bytes.restype = sz

@@ -37,3 +37,13 @@ def test_invalid_arguments_are_statuses_not_crashes():
     assert lib.tt_fsi_apply(None, None, 1, None, None) == 1
     assert lib.tt_fsi_score_masks(4, 2, None) == 1
     assert lib.tt_fsi_status_string(6) == b"non-finite input"
+
+
+def test_unknown_index_rejected_on_host():
+    """Plan creation validates the index before touching the GPU."""
+    import ctypes
+    import paper_2601_01903_gb300 as fsi
+    lib = fsi.native.load()
+    h = ctypes.c_void_p()
+    assert lib.tt_fsi_plan_create_index(10, 2, 9, 0, 1, ctypes.byref(h)) == 1
+    assert not h.value
