@@ -43,10 +43,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--workload", default="mlp_d20_l3_b16",
-                    choices=["mlp_d20_l3_b16", "uneven_1024", "student"],
+                    choices=["mlp_d20_l3_b16", "uneven_1024", "student", "configs"],
                     help="mlp_d20_l3_b16: the headline batch; uneven_1024: 1024 Moebius-sparse "
                          "games with d in 10..20 and l in 1..3, one persistent launch vs "
-                         "per-game launches vs a CUDA graph of them")
+                         "per-game launches vs a CUDA graph of them; student: the amortised "
+                         "explainer; configs: device time of every single-plan configuration "
+                         "(each arithmetic, order 4, the other indices), one JSON line")
     return ap.parse_args()
 
 
@@ -322,6 +324,77 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_configs(args, rank, world, local_rank):
+    """Device time per call of tt_fsi_apply for each configuration of the
+    build target (inputs resident in HBM, CUDA events on the launching
+    stream, 3 rotating input copies where one copy fits in L2)."""
+    import numpy as np
+    import torch
+    import paper_2601_01903_gb300 as fsi
+    from paper_2601_01903_gb300 import synthetic
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    gens = {}
+
+    def masked(w):
+        v = torch.empty((w.x.shape[0], 1 << w.d), dtype=torch.float64, device=dev)
+        fsi.masked_game_into(w.mlp, torch.as_tensor(w.x, device=dev), torch.as_tensor(w.baseline, device=dev), v)
+        return v
+
+    def inputs(name):
+        if name not in gens:
+            if name == "d8":
+                w = synthetic.workload_mobius_d8()
+                gens[name] = torch.as_tensor(w["v"], device=dev).reshape(1, -1)
+            elif name == "d14":
+                gens[name] = masked(synthetic.workload_mlp_d14())
+            elif name == "d20":
+                gens[name] = masked(synthetic.workload_mlp_d20())
+            elif name == "d24":
+                gens[name] = masked(synthetic.workload_mlp_d24())
+        return gens[name]
+
+    rows = []
+    specs = [("cfg1 Moebius game d=8 l=2 B=1", "d8", 8, 2),
+             ("cfg2 masked MLP d=14 l=2 B=64", "d14", 14, 2),
+             ("cfg3a masked MLP d=20 l=3 B=16", "d20", 20, 3),
+             ("cfg3b masked MLP d=24 l=2 B=1", "d24", 24, 2),
+             ("order 4, masked MLP d=20 B=16", "d20", 20, 4)]
+    for label, key, d, ell in specs:
+        v64 = inputs(key)
+        B = v64.shape[0]
+        for arith in ("exact", "f64", "f32"):
+            for index in (("fsi", "sii", "bii", "stii") if key == "d20" and ell == 3 else ("fsi",)):
+                if index != "fsi" and arith == "f64":
+                    continue
+                v = v64.float() if arith == "f32" else v64
+                copies = [v] + ([v.clone(), v.clone()] if v.numel() * v.element_size() < (256 << 20) else [])
+                plan = fsi.Plan(d, ell, arith, max_batch=B, index=index)
+                out = torch.empty((B, plan.n_scores), dtype=v.dtype, device=dev)
+                reps = max(5, min(200, int(2e8 // (B << d))))
+                for i in range(3):
+                    plan.apply(copies[i % len(copies)], out=out)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for i in range(reps):
+                    plan.apply(copies[i % len(copies)], out=out)
+                e1.record()
+                torch.cuda.synchronize()
+                plan.check()
+                ms = e0.elapsed_time(e1) / reps
+                elem = 4 if arith == "f32" else 8
+                rows.append({"config": label, "index": index, "arith": arith, "d": d, "ell": ell, "B": B,
+                             "ms_per_call": ms, "coalitions_per_s": B * (1 << d) / (ms * 1e-3),
+                             "hbm_frac_of_measured": B * (1 << d) * elem / (ms * 1e-3) / 1e9 / peaks()[0],
+                             "calls_timed": reps})
+                plan.close()
+    if rank == 0:
+        print(json.dumps({"metric": "device time of tt_fsi_apply per configuration", "unit": "coalitions/s",
+                          "n_gpus": 1, "data": "synthetic", "rows": rows}), flush=True)
+
+
 def run_uneven(args, rank, world, local_rank):
     """1024 uneven games: the persistent batched launch (autotuned schedule)
     timed against one tt_fsi_apply per game and against a CUDA graph of
@@ -481,6 +554,8 @@ def main():
             run_uneven(args, rank, world, local_rank)
         elif args.workload == "student":
             run_student(args, rank, world, local_rank)
+        elif args.workload == "configs":
+            run_configs(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:
