@@ -113,13 +113,40 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # inputs
 # ---------------------------------------------------------------------------
-def make_inputs(device):
+def shard_workload(rank: int):
+    """The d=20 masked-MLP workload of one rank: the same model, instances
+    [16 rank, 16 rank + 16) of the seeded instance stream (rank 0 is the
+    named 16-game batch), so ranks explain disjoint instances."""
+    from paper_2601_01903_gb300 import synthetic
+    w = synthetic.workload_mlp_d20()
+    if rank:
+        w.x = synthetic.gaussian_instances(BATCH, D, 2, first=rank * BATCH)
+    return w
+
+
+def max_over_ranks(value: float, device) -> float:
+    """Largest value over all ranks (the job takes as long as its slowest
+    rank); the value itself when no process group is running."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Units all ranks processed per second, over the slowest rank's time."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
+def make_inputs(device, rank: int = 0):
     """16 value vectors of the d=20 masked-MLP workload, float64 on device."""
     import numpy as np
     import torch
-    from paper_2601_01903_gb300 import synthetic
     import paper_2601_01903_gb300 as fsi
-    w = synthetic.workload_mlp_d20()
+    w = shard_workload(rank)
     v = torch.empty((BATCH, 1 << D), dtype=torch.float64, device=device)
     fsi.masked_game_into(w.mlp, torch.as_tensor(w.x, device=device),
                          torch.as_tensor(w.baseline, device=device), v)
@@ -214,7 +241,7 @@ def run_ours(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    v, w = make_inputs(dev)
+    v, w = make_inputs(dev, rank)
     n = 1 << D
     # Three copies of the batch rotate so that every step reads its inputs
     # from HBM (3 x 128 MiB is larger than the 126 MiB L2).
@@ -245,14 +272,10 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ms = start.elapsed_time(stop)
+    ms = max_over_ranks(start.elapsed_time(stop), dev)
     plan.check()
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     ms_per_step = ms / args.steps
-    value = world * BATCH * n / (ms_per_step * 1e-3)
+    value = whole_job_rate(BATCH * n, world, ms_per_step)
 
     # per-kernel device time (tracing events on the launching stream): the
     # fused launch the timed steps ran, and for reference the split schedule
@@ -423,8 +446,10 @@ def run_uneven(args, rank, world, local_rank):
         torch.cuda.synchronize(dev)
         return e0.elapsed_time(e1) / steps
 
+    if world > 1:
+        torch.distributed.barrier()
     with ClockSampler(local_rank) as clocks:
-        ms_p = timed(b.apply, args.steps)
+        ms_p = max_over_ranks(timed(b.apply, args.steps), dev)
     b.check()
     ref_steps = max(3, min(args.steps, 10))
     ms_g = timed(b.apply_per_game, ref_steps)
@@ -436,7 +461,7 @@ def run_uneven(args, rank, world, local_rank):
     if rank != 0:
         return
     line = {
-        "metric": "batched uneven FSI coalitions/s (one persistent launch)", "value": coal / (ms_p * 1e-3),
+        "metric": "batched uneven FSI coalitions/s (one persistent launch)", "value": whole_job_rate(coal, world, ms_p),
         "unit": "coalitions/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_p, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"exact": "int64", "f64": "f64", "f32": "int64"}[args.arith], "data": "synthetic",
