@@ -333,6 +333,22 @@ tt_fsi_status tt_fsi_masked_game_sampled(const tt_fsi_mlp *model, const double *
                                          int K, float *out_dev, struct CUstream_st *stream);
 
 /*
+ * The value function of Section 2.1 on the tensor cores, FP32 out (the label
+ * path of the amortised explainer; tt_fsi_masked_game with float64 is the
+ * parity path).  Layer 2 of the MLP runs as tcgen05 BF16 x BF16 -> FP32
+ * matrix products (activations and W2 rounded to BF16), layers 1 and 3 in
+ * FP32.  Requires h1 = h2 = 128 and the float copies W1f, b1f, W2f, b2f,
+ * W3f.  coal_dev = NULL: every coalition of every instance, out [B, 2^d]
+ * (7 <= d <= 30); else coal_dev [B, K] uint32 masks (d <= 32), out [B, K].
+ * err_dev: a device int the kernel ORs 1 into if a tensor-core wait ran out
+ * (bounded; the caller clears it).  Asynchronous on `stream`;
+ * TT_FSI_ERR_UNSUPPORTED for other widths or d.
+ */
+tt_fsi_status tt_fsi_masked_game_tc(const tt_fsi_mlp *model, const double *x_dev, const double *baseline_dev,
+                                    int64_t B, const unsigned *coal_dev, int K, float *out_dev, int *err_dev,
+                                    struct CUstream_st *stream);
+
+/*
  * Waits for the plan's work on `stream`, then reads and clears the plan's
  * device fault word: TT_FSI_OK if no kernel reported a fault since the last
  * check, else the fault's status (e.g. TT_FSI_ERR_NONFINITE).

@@ -190,6 +190,42 @@ def masked_game_into(mlp, x, baseline, out, stream=None):
     return out
 
 
+def masked_game_tc(mlp, x, baseline, coalitions=None, out=None, stream=None):
+    """Value function on the tensor cores (BF16 layer-2 products, FP32
+    out): every coalition ([B, 2^d]) or, given ``coalitions`` [B, K] uint32
+    masks, those only ([B, K]).  Needs hidden widths 128."""
+    import torch
+    dm = mlp if isinstance(mlp, DeviceMLP) else DeviceMLP(mlp)
+    dev = dm.W1.device
+    x = torch.as_tensor(x).to(device=dev, dtype=torch.float64).contiguous()
+    if x.dim() == 1:
+        x = x.unsqueeze(0)
+    baseline = torch.as_tensor(baseline).to(device=dev, dtype=torch.float64).contiguous()
+    B = x.shape[0]
+    if coalitions is None:
+        shape, cptr, K = (B, 1 << dm.d), None, 0
+    else:
+        c = torch.as_tensor(coalitions)
+        if c.dtype != torch.int32:
+            c = torch.as_tensor(np.ascontiguousarray(np.asarray(coalitions, dtype=np.uint32)).view(np.int32))
+        c = c.to(dev).contiguous()
+        if c.dim() != 2 or c.shape[0] != B:
+            raise ValueError("coalitions must be [B, K]")
+        shape, cptr, K = tuple(c.shape), ctypes.c_void_p(c.data_ptr()), int(c.shape[1])
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=dev)
+    if tuple(out.shape) != shape or out.dtype != torch.float32 or not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous float32 tensor of shape {shape}")
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    _check(native.load().tt_fsi_masked_game_tc(ctypes.byref(dm.struct), ctypes.c_void_p(x.data_ptr()),
+                                               ctypes.c_void_p(baseline.data_ptr()), B, cptr, K,
+                                               ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(err.data_ptr()),
+                                               _stream_ptr(stream)), "tt_fsi_masked_game_tc")
+    if int(err.item()) != 0:
+        raise FsiError(5, "tt_fsi_masked_game_tc")
+    return out
+
+
 def masked_game(mlp, x, baseline, dtype=None, stream=None):
     import torch
     dm = mlp if isinstance(mlp, DeviceMLP) else DeviceMLP(mlp)

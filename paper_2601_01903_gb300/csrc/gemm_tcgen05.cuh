@@ -129,6 +129,7 @@ __device__ __forceinline__ void load_tile(uint32_t tile, const __nv_bfloat16 *G,
     }
 }
 
+#ifndef TTFSI_GEMM_HELPERS_ONLY
 __global__ void __launch_bounds__(THREADS) gemm_bf16_tcgen05(GemmArgs a) {
     extern __shared__ __align__(1024) unsigned char gsm_raw[];
     // 1024-byte alignment of the operand tiles (the swizzle is address based)
@@ -249,5 +250,6 @@ __global__ void __launch_bounds__(THREADS) gemm_bf16_tcgen05(GemmArgs a) {
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
 }
+#endif  // TTFSI_GEMM_HELPERS_ONLY
 
 }  // namespace ttfsi_gemm

@@ -22,7 +22,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import (ARITH, DeviceMLP, FsiError, Plan, _check, _stream_ptr, masked_game_into, native,
+from . import (ARITH, DeviceMLP, FsiError, Plan, _check, _stream_ptr, masked_game_into, masked_game_tc, native,
                num_scores, score_masks)
 from . import synthetic
 
@@ -201,10 +201,15 @@ class Explainer:
     """Teacher model + exact FSI path + student, for one (d, l)."""
 
     def __init__(self, mlp, ell: int, hidden: int = 1024, batch: int = 4096, seed: int = 4,
-                 baseline=None, K: int = 64):
+                 baseline=None, K: int = 64, value_path: str = "tc"):
+        """value_path "tc": the teacher's values for labels and spot checks come
+        from the tensor-core kernel (BF16 layer-2 products, about 0.3 % of
+        max|v|); "f32": from the FP32 CUDA-core kernels.  The fallback of
+        ``explain`` always uses the FP32 kernels."""
         import torch
         self.torch = torch
         self.mlp = DeviceMLP(mlp, "cuda")
+        self.tc = value_path == "tc" and self.mlp.h1 == 128 and self.mlp.h2 == 128 and self.mlp.d >= 7
         self.d, self.ell, self.batch, self.K = self.mlp.d, ell, batch, K
         self.n_out = num_scores(self.d, ell)
         self.baseline = torch.zeros(self.d, dtype=torch.float64, device="cuda") if baseline is None else \
@@ -222,28 +227,37 @@ class Explainer:
         self.coal_pool_dev = torch.as_tensor(self.coal_pool.view(np.int32), device="cuda")
 
     # -- the exact path -----------------------------------------------------
-    def values_at(self, x64, coal: np.ndarray):
-        """Teacher values at given coalitions (FP32), [B, K]."""
-        torch = self.torch
-        lib = _declare()
-        c = torch.as_tensor(np.ascontiguousarray(coal, dtype=np.uint32).view(np.int32), device="cuda")
-        out = torch.empty(c.shape, dtype=torch.float32, device="cuda")
-        _check(lib.tt_fsi_masked_game_sampled(ctypes.byref(self.mlp.struct), _p(x64), _p(self.baseline),
-                                               x64.shape[0], _p(c), c.shape[1], _p(out), _stream_ptr()),
+    def _values_listed(self, x64, c, out, tc):
+        if tc:
+            return masked_game_tc(self.mlp, x64, self.baseline, coalitions=c, out=out)
+        _check(_declare().tt_fsi_masked_game_sampled(ctypes.byref(self.mlp.struct), _p(x64), _p(self.baseline),
+                                                      x64.shape[0], _p(c), c.shape[1], _p(out), _stream_ptr()),
                "tt_fsi_masked_game_sampled")
         return out
 
-    def exact(self, x64):
-        """Exact FSI of the teacher's masked games (value vectors in FP32
-        from the masked-game kernel, widened to FP64, exact transform)."""
+    def values_at(self, x64, coal: np.ndarray):
+        """Teacher values at given coalitions (FP32), [B, K]."""
         torch = self.torch
+        c = torch.as_tensor(np.ascontiguousarray(coal, dtype=np.uint32).view(np.int32), device="cuda")
+        out = torch.empty(c.shape, dtype=torch.float32, device="cuda")
+        return self._values_listed(x64, c, out, self.tc)
+
+    def exact(self, x64, tc=None):
+        """FSI of the teacher's masked games by the exact transform (value
+        vectors in FP32 from the tensor-core or the CUDA-core kernel, widened
+        to FP64)."""
+        torch = self.torch
+        tc = self.tc if tc is None else tc
         n = x64.shape[0]
         out = torch.empty((n, self.n_out), dtype=torch.float64, device="cuda")
         v32 = torch.empty((min(n, self.batch), 1 << self.d), dtype=torch.float32, device="cuda")
         for s in range(0, n, self.batch):
             e = min(n, s + self.batch)
             vv = v32[:e - s]
-            masked_game_into(self.mlp, x64[s:e], self.baseline, vv)
+            if tc:
+                masked_game_tc(self.mlp, x64[s:e], self.baseline, out=vv)
+            else:
+                masked_game_into(self.mlp, x64[s:e], self.baseline, vv)
             self.plan.apply(vv.double(), out=out[s:e])
         self.plan.check()
         return out
@@ -294,9 +308,7 @@ class Explainer:
             e = min(n, s + self.batch)
             c = self.coal_pool_dev[:e - s]
             vcoal = torch.empty(c.shape, dtype=torch.float32, device="cuda")
-            _check(lib.tt_fsi_masked_game_sampled(ctypes.byref(self.mlp.struct), _p(x64[s:e]), _p(self.baseline),
-                                                   e - s, _p(c), self.K, _p(vcoal), _stream_ptr()),
-                   "tt_fsi_masked_game_sampled")
+            self._values_listed(x64[s:e], c, vcoal, self.tc)
             _check(lib.tt_fsi_surrogate_residual(_p(phi[s:e]), e - s, self.n_out, _p(self.masks), _p(c), _p(vcoal),
                                                   self.K, _p(r[s:e]), _stream_ptr()), "tt_fsi_surrogate_residual")
         return r
@@ -330,6 +342,6 @@ class Explainer:
         out = phi.double()
         idx = torch.nonzero(fb).flatten()
         if idx.numel():
-            out[idx] = self.exact(x32[idx].double())
+            out[idx] = self.exact(x32[idx].double(), tc=False)
         return out, fb
 

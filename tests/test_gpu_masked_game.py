@@ -59,3 +59,72 @@ def test_float32_output(oracle_mod):
     v32 = fsi.masked_game(w.mlp, w.x[:2], w.baseline, dtype=torch.float32).cpu().numpy()
     ref = oracle_mod.masked_game(w.mlp, w.x[0], w.baseline)
     assert _rel(v32[0].astype(np.float64), ref) <= 1e-5
+
+
+# ---------------------------------------------------------------------------
+# Tensor-core value function (label path): BF16 layer-2 operands
+# ---------------------------------------------------------------------------
+
+# The emulation below rounds the same operands to BF16, but computes layer 1
+# in float64 where the GPU uses float32: an activation whose two values sit on
+# either side of a BF16 rounding boundary rounds to neighbouring BF16 numbers,
+# and each such one-ulp difference (2^-8 relative) moves v by up to ~2e-4 of
+# max|v| at these widths.  The bound allows a handful of them per coalition.
+TC_EMU_TOL = 5e-3
+TC_EXACT_TOL = 3e-2  # against the float64 forward pass: the BF16 precision of this path
+
+
+def _forward_bf16(mlp, z):
+    """The tensor-core path's arithmetic in float64: layer-1 activations and
+    W2 rounded to bfloat16 (round to nearest even), everything else exact."""
+    from oracle.student import bf16_round, gelu
+    a1 = bf16_round(gelu(z @ mlp.W1.T + mlp.b1))
+    z2 = a1 @ bf16_round(mlp.W2).T + mlp.b2
+    return (gelu(z2) @ np.asarray(mlp.W3).reshape(-1)) + float(np.asarray(mlp.b3).reshape(-1)[0])
+
+
+def _inputs(x, base, masks, d):
+    bits = ((masks[:, None] >> np.arange(d)) & 1).astype(bool)
+    return np.where(bits, x[None, :], base[None, :])
+
+
+@pytest.mark.parametrize("d,B", [(9, 2), (16, 2), (20, 1)])
+def test_tensor_core_every_coalition(oracle_mod, d, B):
+    mlp = synthetic.random_mlp(d, 128, 128, seed=40 + d)
+    mlp.b1[:] = 0.05
+    mlp.b2[:] = -0.1
+    x = synthetic.gaussian_instances(B, d, seed=d)
+    base = synthetic.Stream(d, 9).normal(d) * 0.1
+    got = fsi.masked_game_tc(mlp, x, base).cpu().numpy().astype(np.float64)
+    masks = np.arange(1 << d, dtype=np.int64)
+    for b in range(B):
+        if d > 16:  # a sample of rows at d = 20
+            masks = synthetic.Stream(d, 11).integers(0, (1 << d) - 1, 4096).astype(np.int64)
+        ref = _forward_bf16(mlp, _inputs(x[b], base, masks, d))
+        assert _rel(got[b][masks], ref) <= TC_EMU_TOL
+        if d <= 16:
+            assert _rel(got[b], oracle_mod.masked_game(mlp, x[b], base)) <= TC_EXACT_TOL
+
+
+def test_tensor_core_listed_coalitions():
+    d, B, K = 16, 5, 64
+    mlp = synthetic.random_mlp(d, 128, 128, seed=3)
+    x = synthetic.gaussian_instances(B, d, seed=7)
+    base = np.zeros(d)
+    coal = synthetic.Stream(1, 2).integers(0, (1 << d) - 1, B * K).astype(np.uint32).reshape(B, K)
+    got = fsi.masked_game_tc(mlp, x, base, coalitions=coal).cpu().numpy().astype(np.float64)
+    for b in range(B):
+        ref = _forward_bf16(mlp, _inputs(x[b], base, coal[b].astype(np.int64), d))
+        assert _rel(got[b], ref) <= TC_EMU_TOL
+
+
+def test_tensor_core_path_rejects_other_shapes():
+    mlp = synthetic.random_mlp(10, 64, 64, seed=1)
+    x = synthetic.gaussian_instances(1, 10, seed=1)
+    with pytest.raises(fsi.FsiError) as e:
+        fsi.masked_game_tc(mlp, x, np.zeros(10))
+    assert e.value.status == 2
+    small = synthetic.random_mlp(5, 128, 128, seed=1)
+    with pytest.raises(fsi.FsiError) as e:
+        fsi.masked_game_tc(small, synthetic.gaussian_instances(1, 5, seed=1), np.zeros(5))
+    assert e.value.status == 2
