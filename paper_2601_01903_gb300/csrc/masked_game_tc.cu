@@ -2,20 +2,22 @@
 //
 // v_x(S) = f(z), z_i = x_i for i in S and baseline_i otherwise, f the GELU
 // MLP d -> 128 -> 128 -> 1 (Section 2.1's value function of a model with
-// absent features set to a baseline).  One CTA (4 warps) takes 128
+// absent features set to a baseline).  One CTA (8 warps) takes 128
 // coalitions at a time:
-//   layer 1 (CUDA cores): thread k owns hidden unit k and forms its 128
-//     pre-activations -- for the 128 consecutive coalitions of a dense tile
-//     by walking the 7 low bits in Gray-code order (one add per coalition),
-//     for a list of coalitions by a d-term dot product each -- then GELU,
+//   layer 1 (CUDA cores): for the consecutive coalitions of a dense tile a
+//     thread owns two hidden units and 32 coalitions, walking their 5 low
+//     bits in Gray-code order (one add per coalition and unit, every flip a
+//     compile-time constant); for a list of coalitions threads k and k + 128
+//     own unit k, 64 rows each, by a d-term dot product per row -- then GELU,
 //     rounded to BF16 into shared memory in the 128-byte-swizzled K-major
 //     layout the tensor cores read;
 //   layer 2 (tensor cores): eight tcgen05.mma (M = 128 coalitions, N = 128
 //     units, K = 16 each) of the BF16 activations against W2 (rounded to BF16
 //     once per CTA and kept in shared memory), FP32 accumulators in tensor
 //     memory, completion signalled on an mbarrier (bounded wait);
-//   layer 3 (epilogue): thread r reads accumulator row r with tcgen05.ld and
-//     forms b3 + sum_n W3[n] GELU(acc[n] + b2[n]) in FP32.
+//   layer 3 (epilogue): warps w and w + 4 read accumulator rows 32w..32w+31
+//     (their TMEM lane quarter), columns 0-63 and 64-127, with tcgen05.ld and
+//     form b3 + sum_n W3[n] GELU(acc[n] + b2[n]) in FP32.
 // The BF16 rounding of the layer-2 operands is this path's precision (the
 // float64 kernel in masked_game.cu is the parity path).
 #include <cuda_bf16.h>
@@ -40,7 +42,7 @@ using ttfsi_gemm::smem_u32;
 
 constexpr int ROWS = 128;                  // coalitions per tile (MMA M)
 constexpr int H = 128;                     // hidden width (MMA N and K)
-constexpr int THREADS = 128;
+constexpr int THREADS = 256;  // 8 warps
 constexpr int KB_BYTES = ROWS * 128;       // one 64-wide K block of 128 rows: 16 KB
 constexpr int OPERAND_BYTES = 2 * KB_BYTES;  // K = 128: two blocks
 constexpr int SMEM_BYTES = 2 * OPERAND_BYTES + 1024;
@@ -59,7 +61,23 @@ struct Args {
     int *err;
 };
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// GELU(z) = z Phi(z) with the normal tail by Abramowitz & Stegun, Handbook
+// of Mathematical Functions, formula 7.1.26 (Hastings' approximation of
+// erfc(x) = P(t) exp(-x^2), t = 1 / (1 + p x), x >= 0; absolute error of
+// erf below 1.5e-7, far below the BF16 rounding this path applies next):
+// Phi(z) = 1 - q for z >= 0 and q for z < 0, q = erfc(|z| / sqrt 2) / 2.
+// The reciprocal and the exponential run on the special-function unit.
+__device__ __forceinline__ float gelu(float z) {
+    const float x = fabsf(z) * 0.70710678118654752f;
+    float t;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(fmaf(0.3275911f, x, 1.0f)));
+    float p = fmaf(1.061405429f, t, -1.453152027f);
+    p = fmaf(p, t, 1.421413741f);
+    p = fmaf(p, t, -0.284496736f);
+    p = fmaf(p, t, 0.254829592f);
+    const float q = 0.5f * p * t * __expf(-x * x);
+    return z * (z >= 0.f ? 1.0f - q : q);
+}
 
 // Byte offset of element (row r, column k) of a 128 x 128 BF16 operand in
 // two 128-byte-swizzled K blocks.
@@ -78,11 +96,14 @@ __global__ void __launch_bounds__(THREADS) masked_game_tc_kernel(Args a) {
     __shared__ int s_fail;
     __shared__ float zrow[ROWS][33];             // list mode: each row's input vector
     __shared__ float sb2[H], sw3[H];
-    __shared__ float sdelta[7][THREADS];         // dense mode: w1[k][q] (x_q - baseline_q)
+    __shared__ float sdelta[5][H];               // dense mode: w1[k][q] (x_q - baseline_q)
+    __shared__ float spart[ROWS];                // epilogue: the second half's partial sums
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    sb2[tid] = a.b2[tid];
-    sw3[tid] = a.W3[tid];
+    if (tid < H) {
+        sb2[tid] = a.b2[tid];
+        sw3[tid] = a.W3[tid];
+    }
     // W2 -> BF16 B operand (once per CTA)
     for (int i = tid; i < H * H; i += THREADS) {
         const int n = i / H, k = i - n * H;
@@ -104,8 +125,8 @@ __global__ void __launch_bounds__(THREADS) masked_game_tc_kernel(Args a) {
     const uint32_t idesc = ttfsi_gemm::instr_desc_bf16(ROWS, H);
     const uint32_t a_base = smem_u32(aA), b_base = smem_u32(wB);
 
-    // this thread's hidden unit k = tid: its row of W1 and its bias
-    const int k = tid;
+    // list mode: this thread's hidden unit k and half of the tile's rows
+    const int k = tid & (H - 1), half = tid >> 7;
     float w1[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) w1[i] = (i < a.d) ? a.W1[k * a.d + i] : 0.f;
@@ -116,30 +137,50 @@ __global__ void __launch_bounds__(THREADS) masked_game_tc_kernel(Args a) {
     for (long long t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
         // ---- layer 1 into the A operand ----
         if (!a.coal) {
+            // thread (unit pair kp, quarter qr of the rows): units 2kp, 2kp + 1,
+            // rows 32 qr .. 32 qr + 31, walked in Gray-code order over their 5
+            // low bits
             const long long inst = t / tiles_per_inst;
             const unsigned c0 = (unsigned)((t - inst * tiles_per_inst) << 7);
             const double *x = a.x + inst * a.d;
-            float pre = bias1;
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                if (i >= a.d) break;
+            const int kp = tid & 63, qr = tid >> 6, k0 = 2 * kp;
+            const unsigned cb = c0 | ((unsigned)qr << 5);
+            float p0 = a.b1[k0], p1 = a.b1[k0 + 1];
+            for (int i = 0; i < a.d; ++i) {
                 const float xi = (float)x[i], bi = (float)a.base[i];
-                if (i < 7) sdelta[i][k] = w1[i] * (xi - bi);
-                pre += w1[i] * ((((c0 >> i) & 1u) != 0u) ? xi : bi);
-            }
-            // Gray-code walk over the 7 low bits: row g = r ^ (r >> 1)
-            unsigned g = 0;
-            for (int r = 0; r < ROWS; ++r) {
-                if (r > 0) {
-                    const int q = __ffs(r) - 1;  // the bit that flips between g(r-1) and g(r)
-                    pre += ((g >> q) & 1u) ? -sdelta[q][k] : sdelta[q][k];
-                    g ^= 1u << q;
+                const float wa = __ldg(a.W1 + k0 * a.d + i), wb = __ldg(a.W1 + (k0 + 1) * a.d + i);
+                if (i < 5 && qr == 0) {
+                    sdelta[i][k0] = wa * (xi - bi);
+                    sdelta[i][k0 + 1] = wb * (xi - bi);
                 }
-                *reinterpret_cast<__nv_bfloat16 *>(aA + operand_offset((int)g, k)) = __float2bfloat16_rn(gelu(pre));
+                const float zi = ((cb >> i) & 1u) ? xi : bi;
+                p0 = fmaf(wa, zi, p0);
+                p1 = fmaf(wb, zi, p1);
+            }
+            __syncthreads();  // sdelta of this tile
+            float da[5], db[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                da[q] = sdelta[q][k0];
+                db[q] = sdelta[q][k0 + 1];
+            }
+            const int row0 = qr << 5;
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                if (r > 0) {
+                    // the bit that flips between gray(r - 1) and gray(r), and its old value
+                    const int q = (r & 1) ? 0 : (r & 2) ? 1 : (r & 4) ? 2 : (r & 8) ? 3 : 4;
+                    const bool was_set = (((r - 1) ^ ((r - 1) >> 1)) >> q) & 1;
+                    p0 += was_set ? -da[q] : da[q];
+                    p1 += was_set ? -db[q] : db[q];
+                }
+                const int row = row0 + (r ^ (r >> 1));
+                *reinterpret_cast<__nv_bfloat162 *>(aA + operand_offset(row, k0)) =
+                    __floats2bfloat162_rn(gelu(p0), gelu(p1));
             }
         } else {
-            // each thread builds one row's input vector
-            {
+            // the first 128 threads build one row's input vector each
+            if (tid < ROWS) {
                 const long long row = t * ROWS + tid;
                 if (row < a.n_rows) {
                     const long long inst = row / a.K;
@@ -151,7 +192,7 @@ __global__ void __launch_bounds__(THREADS) masked_game_tc_kernel(Args a) {
                 }
             }
             __syncthreads();
-            for (int r = 0; r < ROWS; ++r) {
+            for (int r = half * (ROWS / 2); r < (half + 1) * (ROWS / 2); ++r) {
                 float pre = bias1;
 #pragma unroll
                 for (int i = 0; i < 32; ++i)
@@ -181,12 +222,13 @@ __global__ void __launch_bounds__(THREADS) masked_game_tc_kernel(Args a) {
             break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // ---- layer 3 in the epilogue: thread = accumulator row ----
-        float v = a.b3;
+        // ---- layer 3 in the epilogue: warps w, w + 4 share accumulator rows ----
+        const int quarter = warp & 3, col0 = (warp >> 2) * (H / 2);
+        float v = 0.f;
 #pragma unroll 1
-        for (int c0 = 0; c0 < H; c0 += 16) {
+        for (int c0 = col0; c0 < col0 + H / 2; c0 += 16) {
             uint32_t r[16];
-            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+            const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0;
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
                 "[%16];"
@@ -198,8 +240,10 @@ __global__ void __launch_bounds__(THREADS) masked_game_tc_kernel(Args a) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) v += sw3[c0 + j] * gelu(__uint_as_float(r[j]) + sb2[c0 + j]);
         }
-        const long long row = t * ROWS + 32 * warp + lane;
-        if (row < a.n_rows) a.out[row] = v;
+        if (warp >= 4) spart[32 * quarter + lane] = v;
+        __syncthreads();
+        const long long row = t * ROWS + 32 * quarter + lane;
+        if (warp < 4 && row < a.n_rows) a.out[row] = a.b3 + v + spart[32 * quarter + lane];
         // the accumulators and the A operand are rewritten by the next tile
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();

@@ -202,10 +202,10 @@ class Explainer:
 
     def __init__(self, mlp, ell: int, hidden: int = 1024, batch: int = 4096, seed: int = 4,
                  baseline=None, K: int = 64, value_path: str = "tc"):
-        """value_path "tc": the teacher's values for labels and spot checks come
-        from the tensor-core kernel (BF16 layer-2 products, about 0.3 % of
-        max|v|); "f32": from the FP32 CUDA-core kernels.  The fallback of
-        ``explain`` always uses the FP32 kernels."""
+        """value_path "tc": the teacher's values for labels, spot checks and the
+        fallback of ``explain`` come from the tensor-core kernel (BF16
+        layer-2 products, about 0.3 % of max|v|); "f32": from the FP32
+        CUDA-core kernels."""
         import torch
         self.torch = torch
         self.mlp = DeviceMLP(mlp, "cuda")
@@ -342,6 +342,6 @@ class Explainer:
         out = phi.double()
         idx = torch.nonzero(fb).flatten()
         if idx.numel():
-            out[idx] = self.exact(x32[idx].double(), tc=False)
+            out[idx] = self.exact(x32[idx].double())
         return out, fb
 
