@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--arith", default="exact", choices=["exact", "f64", "f32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--epochs", type=int, default=200, help="student mode: training epochs")
     ap.add_argument("--workload", default="mlp_d20_l3_b16",
                     choices=["mlp_d20_l3_b16", "uneven_1024", "student", "configs"],
                     help="mlp_d20_l3_b16: the headline batch; uneven_1024: 1024 Moebius-sparse "
@@ -490,7 +491,7 @@ def run_student(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     H, BATCH_S, N_TRAIN, N_HELD = 1024, 4096, 200_000, 10_000
-    epochs = max(1, args.steps)
+    epochs = max(1, args.epochs)
     ex = st.Explainer(synthetic.workload_student_teacher(), ell=2, hidden=H, batch=BATCH_S)
     t0 = time.perf_counter()
     train = ex.dataset(N_TRAIN, first=0)

@@ -3,7 +3,8 @@
 //
 //   C[M, N] = A[M, K] . B[N, K]^T      (both operands K-major, row-major in HBM)
 //
-// One CTA (4 warps) computes a 128 x BN tile.  Operand tiles of 128 x 64
+// One CTA (4 warps) computes a 128 x BN tile (of one K slice when K is
+// split over the grid's third dimension).  Operand tiles of 128 x 64
 // bf16 are staged in shared memory in the 128-byte swizzled K-major layout
 // (row r at r * 128 bytes, its 16-byte chunk c at chunk c ^ (r & 7)), two
 // stages deep: cp.async fills stage s + 1 while the tensor cores read stage
@@ -11,8 +12,9 @@
 // an mbarrier; every wait on an mbarrier is bounded and, when it runs out,
 // records an error, drains and returns.  The epilogue reads the accumulator
 // rows back with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile rows
-// 32w..32w+31) and applies bias, GELU or a GELU-derivative factor, writing
-// FP32 and/or BF16 outputs, optionally also transposed.
+// 32w..32w+31), stages them through shared memory so that every global
+// store is coalesced, and applies bias, GELU or a GELU-derivative factor,
+// writing FP32 and/or BF16 outputs, optionally also transposed.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -48,6 +50,11 @@ struct GemmArgs {
     __nv_bfloat16 *Ct;         // BF16 result transposed ([N, M]), or null
     int ldct;
     int *err;
+    // split K: CTA z of the grid's third dimension takes K blocks
+    // [z kbc, (z + 1) kbc) and writes its raw FP32 partial product to
+    // Cf + z cf_zstride (only Cf; the caller adds the slices); kbc = 0: all of K
+    int kbc;
+    long long cf_zstride;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -107,12 +114,36 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool v
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(n) : "memory");
 }
 
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// The normal distribution function Phi(z) and density phi(z) for GELU and
+// its derivative.  The tail q = erfc(|z| / sqrt 2) / 2 follows Abramowitz &
+// Stegun, Handbook of Mathematical Functions, formula 7.1.26 (Hastings'
+// approximation erfc(x) = P(t) exp(-x^2), t = 1 / (1 + p x); absolute error
+// of erf below 1.5e-7, under the BF16 rounding of the activations); the
+// reciprocal and the exponential run on the special-function unit.
+__device__ __forceinline__ void normal_cdf_pdf(float z, float &cdf, float &pdf) {
+    const float x = fabsf(z) * 0.70710678118654752f;
+    float t;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(fmaf(0.3275911f, x, 1.0f)));
+    float p = fmaf(1.061405429f, t, -1.453152027f);
+    p = fmaf(p, t, 1.421413741f);
+    p = fmaf(p, t, -0.284496736f);
+    p = fmaf(p, t, 0.254829592f);
+    const float e = __expf(-x * x);  // exp(-z^2 / 2)
+    const float q = 0.5f * p * t * e;
+    cdf = z >= 0.f ? 1.0f - q : q;
+    pdf = 0.39894228040143268f * e;
+}
+
+__device__ __forceinline__ float gelu_f(float z) {
+    float cdf, pdf;
+    normal_cdf_pdf(z, cdf, pdf);
+    return z * cdf;
+}
 
 __device__ __forceinline__ float gelu_grad_f(float z) {
     // d/dz [z Phi(z)] = Phi(z) + z phi(z)
-    const float cdf = 0.5f * (1.0f + erff(z * 0.70710678118654752f));
-    const float pdf = 0.39894228040143268f * __expf(-0.5f * z * z);
+    float cdf, pdf;
+    normal_cdf_pdf(z, cdf, pdf);
     return cdf + z * pdf;
 }
 
@@ -141,7 +172,10 @@ __global__ void __launch_bounds__(THREADS) gemm_bf16_tcgen05(GemmArgs a) {
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int nk = (a.K + BK - 1) / BK;
+    const int nk_all = (a.K + BK - 1) / BK;
+    const int kb0 = a.kbc > 0 ? (int)blockIdx.z * a.kbc : 0;
+    const int nk = a.kbc > 0 ? min(a.kbc, nk_all - kb0) : nk_all;  // K blocks of this CTA
+    float *const Cf = a.Cf ? a.Cf + (long long)blockIdx.z * a.cf_zstride : nullptr;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(smem_u32(&mbar[s]), 1);
@@ -165,8 +199,8 @@ __global__ void __launch_bounds__(THREADS) gemm_bf16_tcgen05(GemmArgs a) {
     bool fail = false;
 
     // prologue: stage 0
-    load_tile(tileA(0), a.A, a.lda, m0, a.M, 0, a.K);
-    load_tile(tileB(0), a.B, a.ldb, n0, a.N, 0, a.K);
+    load_tile(tileA(0), a.A, a.lda, m0, a.M, kb0 * BK, a.K);
+    load_tile(tileB(0), a.B, a.ldb, n0, a.N, kb0 * BK, a.K);
     asm volatile("cp.async.commit_group;" ::: "memory");
 
     for (int kb = 0; kb < nk && !fail; ++kb) {
@@ -179,8 +213,8 @@ __global__ void __launch_bounds__(THREADS) gemm_bf16_tcgen05(GemmArgs a) {
                 issued_bits &= ~(1u << sn);
             }
             if (!fail) {
-                load_tile(tileA(sn), a.A, a.lda, m0, a.M, (kb + 1) * BK, a.K);
-                load_tile(tileB(sn), a.B, a.ldb, n0, a.N, (kb + 1) * BK, a.K);
+                load_tile(tileA(sn), a.A, a.lda, m0, a.M, (kb0 + kb + 1) * BK, a.K);
+                load_tile(tileB(sn), a.B, a.ldb, n0, a.N, (kb0 + kb + 1) * BK, a.K);
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
             asm volatile("cp.async.wait_group 1;" ::: "memory");
@@ -194,7 +228,7 @@ __global__ void __launch_bounds__(THREADS) gemm_bf16_tcgen05(GemmArgs a) {
         if (fail) break;
         if (threadIdx.x == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int kmax = min(BK, a.K - kb * BK);
+            const int kmax = min(BK, a.K - (kb0 + kb) * BK);
             for (int k16 = 0; k16 * 16 < kmax; ++k16) {
                 const uint64_t da = smem_desc(tileA(s) + k16 * 32);
                 const uint64_t db = smem_desc(tileB(s) + k16 * 32);
@@ -215,10 +249,16 @@ __global__ void __launch_bounds__(THREADS) gemm_bf16_tcgen05(GemmArgs a) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
     if (!s_fail) {
-        // epilogue: rows m0 + 32 * warp + lane, 16 columns at a time
-        const int row = m0 + 32 * warp + lane;
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            uint32_t r[16];
+        // Epilogue, 32 columns at a time.  Warp w owns accumulator rows
+        // 32w..32w+31 (its TMEM lane quarter); tcgen05.ld gives each lane one
+        // row, so the values go through a per-warp 32 x 33 staging block in
+        // the (now idle) operand tiles and leave with lanes over columns
+        // (row-major outputs) or over rows (the transposed output), i.e. as
+        // coalesced stores.
+        float *stage = reinterpret_cast<float *>(gsm_raw + (base - raw)) + warp * (32 * 33);
+        const int rbase = m0 + 32 * warp;
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            uint32_t r[32];
             const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
@@ -227,21 +267,55 @@ __global__ void __launch_bounds__(THREADS) gemm_bf16_tcgen05(GemmArgs a) {
                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
                   "=r"(r[15])
                 : "r"(taddr));
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+                  "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                  "=r"(r[30]), "=r"(r[31])
+                : "r"(taddr + 16u));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row >= a.M) continue;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int col = n0 + c0 + j;
-                if (col >= a.N) continue;
-                float z = __uint_as_float(r[j]);
-                if (a.bias) z += a.bias[col];
-                if (a.dgelu_z) z *= gelu_grad_f(a.dgelu_z[(long long)row * a.ldz + col]);
-                if (a.Cf) a.Cf[(long long)row * a.ldcf + col] = z;
-                const float y = (a.act == 1) ? gelu_f(z) : z;
-                const __nv_bfloat16 yb = __float2bfloat16_rn(y);
-                if (a.Cb) a.Cb[(long long)row * a.ldcb + col] = yb;
-                if (a.Ct) a.Ct[(long long)col * a.ldct + row] = yb;
+            for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(r[j]);
+            __syncwarp();
+            // row pass: lane = column; the pre-activations of the GELU factor
+            // are loaded 8 rows at a time ahead of their use, so the loads overlap
+            const int col = n0 + c0 + lane;
+            const bool col_ok = col < a.N;
+            const float bias = (a.bias && col_ok) ? a.bias[col] : 0.f;
+#pragma unroll 1
+            for (int i0 = 0; i0 < 32; i0 += 8) {
+                float zin[8];
+                if (a.dgelu_z) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        zin[i] = (col_ok && rbase + i0 + i < a.M) ? a.dgelu_z[(long long)(rbase + i0 + i) * a.ldz + col]
+                                                                  : 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int row = rbase + i0 + i;
+                    if (row < a.M && col_ok) {
+                        float z = stage[(i0 + i) * 33 + lane] + bias;
+                        if (a.dgelu_z) z *= gelu_grad_f(zin[i]);
+                        if (Cf) Cf[(long long)row * a.ldcf + col] = z;
+                        const float y = (a.act == 1) ? gelu_f(z) : z;
+                        if (a.Cb) a.Cb[(long long)row * a.ldcb + col] = __float2bfloat16_rn(y);
+                        stage[(i0 + i) * 33 + lane] = y;
+                    }
+                }
             }
+            if (a.Ct) {
+                __syncwarp();
+                // column pass: lane = row
+                const int row = rbase + lane;
+                if (row < a.M)
+                    for (int j = 0; j < 32; ++j) {
+                        const int colj = n0 + c0 + j;
+                        if (colj < a.N) a.Ct[(long long)colj * a.ldct + row] = __float2bfloat16_rn(stage[lane * 33 + j]);
+                    }
+            }
+            __syncwarp();
         }
     } else if (threadIdx.x == 0) {
         atomicOr(a.err, kErrGemmTimeout);

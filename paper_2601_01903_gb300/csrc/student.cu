@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "gemm_tcgen05.cuh"
 #include "tt_fsi.h"
 
@@ -27,9 +29,35 @@ tt_fsi_status gemm_launch(const ttfsi_gemm::GemmArgs &a, cudaStream_t st) {
         if (e != cudaSuccess) return st_status(e);
         g_gemm_attr_set[dev] = true;
     }
-    dim3 grid((unsigned)((a.N + BN - 1) / BN), (unsigned)((a.M + BM - 1) / BM));
+    const int nk = (a.K + BK - 1) / BK;
+    const int kslices = a.kbc > 0 ? (nk + a.kbc - 1) / a.kbc : 1;
+    dim3 grid((unsigned)((a.N + BN - 1) / BN), (unsigned)((a.M + BM - 1) / BM), (unsigned)kslices);
     gemm_bf16_tcgen05<<<grid, THREADS, SMEM_BYTES, st>>>(a);
     return st_status(cudaGetLastError());
+}
+
+// Sum of the K-slice partial products in slice order, plus an optional bias
+// per column: C[r, c] = sum_z P_z[r, c] (+ bias[c]).
+__global__ void ksum_kernel(const float *part, long long zstride, int slices, int M, int N, int ld, const float *bias,
+                            float *C) {
+    const long long n = (long long)M * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / N, c = i - r * N;
+        float s = 0.f;
+        for (int z = 0; z < slices; ++z) s += part[z * zstride + r * ld + c];
+        C[r * ld + c] = bias ? s + bias[c] : s;
+    }
+}
+
+// K blocks per slice for a plain (Cf-only) product: split K when the output
+// tiles alone cannot fill the GPU, keeping at least 4 K blocks per slice.
+int split_kbc(int M, int N, int K) {
+    const int tiles = ((M + ttfsi_gemm::BM - 1) / ttfsi_gemm::BM) * ((N + ttfsi_gemm::BN - 1) / ttfsi_gemm::BN);
+    const int nk = (K + ttfsi_gemm::BK - 1) / ttfsi_gemm::BK;
+    if (tiles >= 128 || nk < 8) return 0;
+    int slices = std::min((2 * 152 + tiles - 1) / tiles, nk / 4);
+    if (slices < 2) return 0;
+    return (nk + slices - 1) / slices;
 }
 
 }  // namespace
@@ -78,26 +106,26 @@ namespace ttfsi_student {
 using bf16 = __nv_bfloat16;
 constexpr int kErrTimeout = 1;
 
-__global__ void x_to_bf16_kernel(const float *x, int B, int d, bf16 *xb, bf16 *xbt, int ldt) {
-    const long long n = (long long)B * d;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(i / d), j = (int)(i - (long long)b * d);
-        const bf16 v = __float2bfloat16_rn(x[i]);
-        xb[i] = v;
-        if (xbt) xbt[(long long)j * ldt + b] = v;
+// FP32 [rows, cols] (row-major) -> BF16 copy Wb [rows_pad, cols] (rows >= rows
+// zero; optional) and transposed BF16 copy Wt [cols, ldt] with Wt[c][r] =
+// W[r][c] for r < rows_pad (zero for r >= rows; optional), through 32 x 32
+// shared-memory tiles so that the reads and both writes are coalesced.
+// Block 32 x 8 threads, grid (ceil(cols / 32), ceil(rows_pad / 32)).
+__global__ void to_bf16_tiled_kernel(const float *W, int rows, int cols, int rows_pad, bf16 *Wb, bf16 *Wt, int ldt) {
+    __shared__ float tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int i = ty; i < 32; i += 8) {
+        const int r = r0 + i, c = c0 + tx;
+        const float w = (r < rows && c < cols) ? W[(long long)r * cols + c] : 0.0f;
+        tile[i][tx] = w;
+        if (Wb && r < rows_pad && c < cols) Wb[(long long)r * cols + c] = __float2bfloat16_rn(w);
     }
-}
-
-// BF16 copies of the FP32 weights: W [rows, cols] -> Wb [rows_pad, cols]
-// (rows >= rows zero) and optionally Wt [cols, ldt] = W^T (columns >= rows zero).
-__global__ void weights_to_bf16_kernel(const float *W, int rows, int cols, int rows_pad, bf16 *Wb, bf16 *Wt, int ldt) {
-    const long long n = (long long)rows_pad * cols;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(i / cols), c = (int)(i - (long long)r * cols);
-        const float w = (r < rows) ? W[(long long)r * cols + c] : 0.0f;
-        const bf16 v = __float2bfloat16_rn(w);
-        Wb[i] = v;
-        if (Wt) Wt[(long long)c * ldt + r] = v;
+    if (!Wt) return;
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        const int c = c0 + i, r = r0 + tx;
+        if (c < cols && r < rows_pad) Wt[(long long)c * ldt + r] = __float2bfloat16_rn(tile[tx][i]);
     }
 }
 
@@ -142,16 +170,38 @@ __global__ void project_loss_kernel(const float *Y, int B, int n_out, const floa
         if (k < n_out) dYf[(long long)warp * n_out + k] = g;
         const bf16 gb = __float2bfloat16_rn(g);
         dYb[(long long)warp * ld_dyb + k] = gb;
-        if (k < n_out) dYt[(long long)k * ld_dyt + warp] = gb;
+        if (dYt && k < n_out) dYt[(long long)k * ld_dyt + warp] = gb;
     }
 }
 
-// Column sums of an FP32 [M, N] matrix, one thread per column, fixed order.
-__global__ void colsum_kernel(const float *X, int M, int N, float *out) {
+// Column sums of an FP32 [M, N] matrix in a fixed order, in two passes.
+// Pass 1: block (32 columns, a slab of 256 rows), 32 x 8 threads; thread
+// (x, y) sums rows 32y..32y+31 of the slab, the 8 partials are added in order
+// and written to part[slab][N].  Pass 2: one thread per column adds the slab
+// partials in order.
+__global__ void colsum_partial_kernel(const float *X, int M, int N, float *part) {
+    __shared__ float red[8][33];
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    const int r0 = blockIdx.y * 256 + threadIdx.y * 32;
+    float s = 0.f;
+    if (c < N) {
+        const int r1 = min(r0 + 32, M);
+        for (int r = r0; r < r1; ++r) s += X[(long long)r * N + c];
+    }
+    red[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < N) {
+        float t = 0.f;
+        for (int k = 0; k < 8; ++k) t += red[k][threadIdx.x];
+        part[(long long)blockIdx.y * N + c] = t;
+    }
+}
+
+__global__ void colsum_final_kernel(const float *part, int slabs, int N, float *out) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     float s = 0.f;
-    for (int r = 0; r < M; ++r) s += X[(long long)r * N + c];
+    for (int k = 0; k < slabs; ++k) s += part[(long long)k * N + c];
     out[c] = s;
 }
 
@@ -221,6 +271,8 @@ struct tt_fsi_student_s {
     __nv_bfloat16 *dYb = nullptr, *dYt = nullptr, *dH2 = nullptr, *dH2T = nullptr, *dH1T = nullptr;
     float *Z1 = nullptr, *Z2 = nullptr, *Y = nullptr, *dYf = nullptr, *dH2f = nullptr, *dH1f = nullptr;
     float *loss_rows = nullptr;
+    float *colpart = nullptr;  // column-sum partials [ceil(max_batch / 256)][max(H, n_out)]
+    float *gpart = nullptr;    // K-slice partial products of the weight gradients
     int *err = nullptr;
     float lr = 1e-3f, beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
     long long step = 0;
@@ -243,7 +295,7 @@ cudaError_t st_alloc(tt_fsi_student_s *s, T **p, size_t count) {
 
 tt_fsi_status gemm(const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N, int K, const float *bias, int act,
                    const float *dz, int ldz, float *Cf, int ldcf, bf16 *Cb, int ldcb, bf16 *Ct, int ldct, int *err,
-                   cudaStream_t st) {
+                   cudaStream_t st, float *gpart = nullptr) {
     ttfsi_gemm::GemmArgs a{};
     a.A = A;
     a.B = B;
@@ -263,17 +315,42 @@ tt_fsi_status gemm(const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N,
     a.Ct = Ct;
     a.ldct = ldct;
     a.err = err;
+    // plain products with a long K (the weight gradients) are split over K
+    // into the student's partial buffer and summed in slice order
+    const int kbc = (!act && !dz && !Cb && !Ct && Cf && gpart) ? split_kbc(M, N, K) : 0;
+    if (kbc > 0) {
+        const int nk = (K + ttfsi_gemm::BK - 1) / ttfsi_gemm::BK, slices = (nk + kbc - 1) / kbc;
+        a.kbc = kbc;
+        a.bias = nullptr;  // added once, in the slice sum
+        a.Cf = gpart;
+        a.cf_zstride = (long long)M * ldcf;
+        tt_fsi_status r = gemm_launch(a, st);
+        if (r != TT_FSI_OK) return r;
+        const long long n = (long long)M * N;
+        ksum_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, st>>>(gpart, a.cf_zstride, slices, M,
+                                                                                          N, ldcf, bias, Cf);
+        return st_status(cudaGetLastError());
+    }
     return gemm_launch(a, st);
 }
 
+void to_bf16(const float *W, int rows, int cols, int rows_pad, bf16 *Wb, bf16 *Wt, int ldt, cudaStream_t st) {
+    const dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows_pad + 31) / 32));
+    ttfsi_student::to_bf16_tiled_kernel<<<grid, dim3(32, 8), 0, st>>>(W, rows, cols, rows_pad, Wb, Wt, ldt);
+}
+
+// Bias gradient: column sums of an FP32 [M, N] matrix (fixed order).
+void colsum(tt_fsi_student_s *s, const float *X, int M, int N, float *out, cudaStream_t st) {
+    const int slabs = (M + 255) / 256;
+    ttfsi_student::colsum_partial_kernel<<<dim3((unsigned)((N + 31) / 32), (unsigned)slabs), dim3(32, 8), 0, st>>>(
+        X, M, N, s->colpart);
+    ttfsi_student::colsum_final_kernel<<<(N + 127) / 128, 128, 0, st>>>(s->colpart, slabs, N, out);
+}
+
 tt_fsi_status refresh_bf16(tt_fsi_student_s *s, cudaStream_t st) {
-    using namespace ttfsi_student;
-    weights_to_bf16_kernel<<<grid_for((long long)s->H * s->d), 256, 0, st>>>(s->params + s->off_W1, s->H, s->d, s->H,
-                                                                           s->W1b, nullptr, 0);
-    weights_to_bf16_kernel<<<grid_for((long long)s->H * s->H), 256, 0, st>>>(s->params + s->off_W2, s->H, s->H, s->H,
-                                                                           s->W2b, s->W2bT, s->H);
-    weights_to_bf16_kernel<<<grid_for((long long)s->n_pad * s->H), 256, 0, st>>>(
-        s->params + s->off_W3, s->n_out, s->H, s->n_pad, s->W3b, s->W3bT, s->n_pad);
+    to_bf16(s->params + s->off_W1, s->H, s->d, s->H, s->W1b, nullptr, 0, st);
+    to_bf16(s->params + s->off_W2, s->H, s->H, s->H, s->W2b, s->W2bT, s->H, st);
+    to_bf16(s->params + s->off_W3, s->n_out, s->H, s->n_pad, s->W3b, s->W3bT, s->n_pad, st);
     return st_status(cudaGetLastError());
 }
 
@@ -281,7 +358,7 @@ tt_fsi_status refresh_bf16(tt_fsi_student_s *s, cudaStream_t st) {
 // pass needs (transposed activations).
 tt_fsi_status forward(tt_fsi_student_s *s, const float *x, int B, bool train, cudaStream_t st) {
     using namespace ttfsi_student;
-    x_to_bf16_kernel<<<grid_for((long long)B * s->d), 256, 0, st>>>(x, B, s->d, s->Xb, train ? s->XbT : nullptr, s->ldB);
+    to_bf16(x, B, s->d, B, s->Xb, train ? s->XbT : nullptr, s->ldB, st);
     tt_fsi_status r = st_status(cudaGetLastError());
     if (r != TT_FSI_OK) return r;
     const float *P = s->params;
@@ -292,7 +369,7 @@ tt_fsi_status forward(tt_fsi_student_s *s, const float *x, int B, bool train, cu
              train ? s->A2T : nullptr, s->ldB, s->err, st);
     if (r != TT_FSI_OK) return r;
     return gemm(s->A2, s->H, s->W3b, s->H, B, s->n_out, s->H, P + s->off_b3, 0, nullptr, 0, s->Y, s->n_out, nullptr, 0,
-                nullptr, 0, s->err, st);
+                nullptr, 0, s->err, st, s->gpart);
 }
 
 // Gradients of the mean squared error of the projected outputs into s->grads.
@@ -301,31 +378,33 @@ tt_fsi_status backward(tt_fsi_student_s *s, const float *labels, const float *ta
     using namespace ttfsi_student;
     const int warps_per_block = 8;
     project_loss_kernel<<<(B + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
-        s->Y, B, s->n_out, target, v_empty, nullptr, labels, s->loss_rows, s->dYf, s->dYb, s->n_pad, s->dYt, s->ldB);
+        s->Y, B, s->n_out, target, v_empty, nullptr, labels, s->loss_rows, s->dYf, s->dYb, s->n_pad, nullptr, 0);
+    // dY^T (rows n_out..n_pad of dYt stay zero)
+    to_bf16(s->dYf, B, s->n_out, B, nullptr, s->dYt, s->ldB, st);
     tt_fsi_status r = st_status(cudaGetLastError());
     if (r != TT_FSI_OK) return r;
     if (loss_dev) sum_kernel<<<1, 256, 0, st>>>(s->loss_rows, B, 1.0f / ((float)B * s->n_out), loss_dev);
     float *G = s->grads;
     // layer 3
     r = gemm(s->dYt, s->ldB, s->A2T, s->ldB, s->n_out, s->H, B, nullptr, 0, nullptr, 0, G + s->off_W3, s->H, nullptr, 0,
-             nullptr, 0, s->err, st);
+             nullptr, 0, s->err, st, s->gpart);
     if (r != TT_FSI_OK) return r;
-    colsum_kernel<<<(s->n_out + 127) / 128, 128, 0, st>>>(s->dYf, B, s->n_out, G + s->off_b3);
+    colsum(s, s->dYf, B, s->n_out, G + s->off_b3, st);
     r = gemm(s->dYb, s->n_pad, s->W3bT, s->n_pad, B, s->H, s->n_pad, nullptr, 0, s->Z2, s->H, s->dH2f, s->H, s->dH2,
              s->H, s->dH2T, s->ldB, s->err, st);
     if (r != TT_FSI_OK) return r;
     // layer 2
-    colsum_kernel<<<(s->H + 127) / 128, 128, 0, st>>>(s->dH2f, B, s->H, G + s->off_b2);
+    colsum(s, s->dH2f, B, s->H, G + s->off_b2, st);
     r = gemm(s->dH2T, s->ldB, s->A1T, s->ldB, s->H, s->H, B, nullptr, 0, nullptr, 0, G + s->off_W2, s->H, nullptr, 0,
-             nullptr, 0, s->err, st);
+             nullptr, 0, s->err, st, s->gpart);
     if (r != TT_FSI_OK) return r;
     r = gemm(s->dH2, s->H, s->W2bT, s->H, B, s->H, s->H, nullptr, 0, s->Z1, s->H, s->dH1f, s->H, nullptr, 0, s->dH1T,
              s->ldB, s->err, st);
     if (r != TT_FSI_OK) return r;
     // layer 1
-    colsum_kernel<<<(s->H + 127) / 128, 128, 0, st>>>(s->dH1f, B, s->H, G + s->off_b1);
+    colsum(s, s->dH1f, B, s->H, G + s->off_b1, st);
     r = gemm(s->dH1T, s->ldB, s->XbT, s->ldB, s->H, s->d, B, nullptr, 0, nullptr, 0, G + s->off_W1, s->d, nullptr, 0,
-             nullptr, 0, s->err, st);
+             nullptr, 0, s->err, st, s->gpart);
     if (r != TT_FSI_OK) return r;
     return st_status(cudaGetLastError());
 }
@@ -398,6 +477,22 @@ tt_fsi_status tt_fsi_student_create(int d, int hidden, int n_out, int max_batch,
     A(&s->dH1f, Bm * H);
     A(&s->dH1T, H * Bm);
     A(&s->loss_rows, Bm);
+    A(&s->colpart, ((Bm + 255) / 256) * (size_t)std::max(hidden, n_out));
+    {
+        // the largest split product: the weight gradients W3 [n_out, H], W2 [H, H], W1 [H, d] with
+        // K = max_batch
+        size_t need = 0;
+        // (and the forward output layer [max_batch, n_out] with K = H)
+        const int shapes[4][3] = {{n_out, hidden, max_batch}, {hidden, hidden, max_batch}, {hidden, d, max_batch},
+                                  {max_batch, n_out, hidden}};
+        for (auto &sh : shapes) {
+            const int kbc = split_kbc(sh[0], sh[1], sh[2]);
+            if (!kbc) continue;
+            const int nk = (sh[2] + ttfsi_gemm::BK - 1) / ttfsi_gemm::BK;
+            need = std::max(need, (size_t)((nk + kbc - 1) / kbc) * sh[0] * sh[1]);
+        }
+        if (need) A(&s->gpart, need);
+    }
     A(&s->err, 1);
     if (e == cudaSuccess) e = cudaMemcpy(s->params, params_host, (size_t)o * sizeof(float), cudaMemcpyHostToDevice);
     tt_fsi_status r = st_status(e);
