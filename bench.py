@@ -44,12 +44,13 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--epochs", type=int, default=200, help="student mode: training epochs")
     ap.add_argument("--workload", default="mlp_d20_l3_b16",
-                    choices=["mlp_d20_l3_b16", "uneven_1024", "student", "configs"],
+                    choices=["mlp_d20_l3_b16", "uneven_1024", "student", "configs", "value_function"],
                     help="mlp_d20_l3_b16: the headline batch; uneven_1024: 1024 Moebius-sparse "
                          "games with d in 10..20 and l in 1..3, one persistent launch vs "
                          "per-game launches vs a CUDA graph of them; student: the amortised "
                          "explainer; configs: device time of every single-plan configuration "
-                         "(each arithmetic, order 4, the other indices), one JSON line")
+                         "(each arithmetic, order 4, the other indices), one JSON line; "
+                         "value_function: the masked-model value function on each path")
     return ap.parse_args()
 
 
@@ -419,6 +420,54 @@ def run_configs(args, rank, world, local_rank):
                           "n_gpus": 1, "data": "synthetic", "rows": rows}), flush=True)
 
 
+def run_value_function(args, rank, world, local_rank):
+    """Device time of the value function v_x(S) for every coalition: float64
+    and float32 CUDA-core kernels, the tensor-core kernel, and the
+    interventional value function with 100 background rows (Section 4.1) on
+    the tensor cores.  Models 16-128-128-1 (64 instances) and 20-128-128-1
+    (16 instances), random init; the value function is input generation for
+    the FSI path and is not part of its timed step."""
+    import torch
+    import paper_2601_01903_gb300 as fsi
+    from paper_2601_01903_gb300 import synthetic
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    rows = []
+    for d, B in ((16, 64), (20, 16)):
+        mlp = fsi.DeviceMLP(synthetic.random_mlp(d, 128, 128, seed=2), dev)
+        x = torch.as_tensor(synthetic.gaussian_instances(B, d, seed=2), device=dev)
+        base = torch.zeros(d, dtype=torch.float64, device=dev)
+        bg = torch.as_tensor(synthetic.gaussian_instances(100, d, seed=7), device=dev)
+        o64 = torch.empty((B, 1 << d), dtype=torch.float64, device=dev)
+        o32 = torch.empty((B, 1 << d), dtype=torch.float32, device=dev)
+
+        def timed(fn, reps):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        paths = [("float64 CUDA cores (parity path)", lambda: fsi.masked_game_into(mlp, x, base, o64), 1, 1),
+                 ("float32 CUDA cores", lambda: fsi.masked_game_into(mlp, x, base, o32), 1, 2),
+                 ("tcgen05 BF16 layer 2", lambda: fsi.masked_game_tc(mlp, x, base, out=o32), 1, 5),
+                 ("tcgen05, interventional, 100 background rows",
+                  lambda: fsi.masked_game_tc(mlp, x, bg, out=o32), 100, 2)]
+        for name, fn, n_bg, reps in paths:
+            ms = timed(fn, reps)
+            rows.append({"d": d, "instances": B, "path": name, "background_rows": n_bg, "ms_per_call": ms,
+                         "model_evaluations_per_s": B * (1 << d) * n_bg / (ms * 1e-3),
+                         "instances_per_s": B / (ms * 1e-3)})
+    if rank == 0:
+        print(json.dumps({"metric": "masked-model value function (all 2^d coalitions) per path",
+                          "unit": "model evaluations/s", "n_gpus": 1, "data": "synthetic", "rows": rows}),
+              flush=True)
+
+
 def run_uneven(args, rank, world, local_rank):
     """1024 uneven games: the persistent batched launch (autotuned schedule)
     timed against one tt_fsi_apply per game and against a CUDA graph of
@@ -588,6 +637,8 @@ def main():
             run_student(args, rank, world, local_rank)
         elif args.workload == "configs":
             run_configs(args, rank, world, local_rank)
+        elif args.workload == "value_function":
+            run_value_function(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

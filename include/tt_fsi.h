@@ -323,6 +323,20 @@ tt_fsi_status tt_fsi_masked_game(const tt_fsi_mlp *model, const double *x_dev,
                                  struct CUstream_st *stream);
 
 /*
+ * The interventional value function of Section 4.1 ("Value Function"):
+ * v[b, S] = (1 / n_background) sum_k f(z^k), z^k_i = x[b, i] for i in S and
+ * background[k, i] otherwise -- the expectation over the absent features,
+ * estimated with n_background rows (100 in the paper's experiments).
+ * background_dev [n_background, d] float64 row-major; layout, types and
+ * stream as tt_fsi_masked_game (which is this call with the baseline as the
+ * single background row).  One launch per background row; the rows are
+ * added in ascending order, so results are deterministic.
+ */
+tt_fsi_status tt_fsi_masked_game_interventional(const tt_fsi_mlp *model, const double *x_dev,
+                                                const double *background_dev, int n_background, int64_t B,
+                                                void *v_dev, int out_f32, struct CUstream_st *stream);
+
+/*
  * The same value function at K given coalitions per instance:
  * out[b, k] = f(z), z_i = x[b, i] if bit i of coal[b, k] is set, else
  * baseline[i]; coal [B, K] uint32 masks (d <= 32), out [B, K] FP32
@@ -347,6 +361,18 @@ tt_fsi_status tt_fsi_masked_game_sampled(const tt_fsi_mlp *model, const double *
 tt_fsi_status tt_fsi_masked_game_tc(const tt_fsi_mlp *model, const double *x_dev, const double *baseline_dev,
                                     int64_t B, const unsigned *coal_dev, int K, float *out_dev, int *err_dev,
                                     struct CUstream_st *stream);
+
+/*
+ * The interventional value function (Section 4.1; see
+ * tt_fsi_masked_game_interventional) on the tensor cores: each tile of
+ * coalitions runs the three layers once per background row and averages in
+ * FP32.  background_dev [n_background, d]; everything else as
+ * tt_fsi_masked_game_tc (which is this call with one background row).
+ */
+tt_fsi_status tt_fsi_masked_game_tc_interventional(const tt_fsi_mlp *model, const double *x_dev,
+                                                   const double *background_dev, int n_background, int64_t B,
+                                                   const unsigned *coal_dev, int K, float *out_dev, int *err_dev,
+                                                   struct CUstream_st *stream);
 
 /*
  * Waits for the plan's work on `stream`, then reads and clears the plan's

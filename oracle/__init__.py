@@ -381,6 +381,19 @@ def masked_game(mlp, x, baseline, coalitions=None) -> np.ndarray:
     return out
 
 
+def masked_game_interventional(mlp, x, background, coalitions=None) -> np.ndarray:
+    """Interventional value function of Section 4.1 ("Value Function"):
+    v(S) = E over the absent features of f(x_S, X_rest), estimated as the
+    mean over the given background rows of the masked game with that row as
+    the reference input (rows added in ascending order); one instance."""
+    bg = np.atleast_2d(np.asarray(background, dtype=np.float64))
+    acc = None
+    for row in bg:
+        v = masked_game(mlp, x, row, coalitions)
+        acc = v if acc is None else acc + v
+    return acc / bg.shape[0]
+
+
 # ---------------------------------------------------------------------------
 # The paper's MPO and sweep (Sections 3.2-3.4, Algorithm 1), explicit states
 # ---------------------------------------------------------------------------

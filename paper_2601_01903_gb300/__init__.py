@@ -193,7 +193,9 @@ def masked_game_into(mlp, x, baseline, out, stream=None):
 def masked_game_tc(mlp, x, baseline, coalitions=None, out=None, stream=None):
     """Value function on the tensor cores (BF16 layer-2 products, FP32
     out): every coalition ([B, 2^d]) or, given ``coalitions`` [B, K] uint32
-    masks, those only ([B, K]).  Needs hidden widths 128."""
+    masks, those only ([B, K]).  Needs hidden widths 128.  ``baseline`` [d]
+    is one reference input; [n, d] are n background rows (the interventional
+    value function: the mean of f over them)."""
     import torch
     dm = mlp if isinstance(mlp, DeviceMLP) else DeviceMLP(mlp)
     dev = dm.W1.device
@@ -217,12 +219,38 @@ def masked_game_tc(mlp, x, baseline, coalitions=None, out=None, stream=None):
     if tuple(out.shape) != shape or out.dtype != torch.float32 or not out.is_contiguous():
         raise ValueError(f"out must be a contiguous float32 tensor of shape {shape}")
     err = torch.zeros(1, dtype=torch.int32, device=dev)
-    _check(native.load().tt_fsi_masked_game_tc(ctypes.byref(dm.struct), ctypes.c_void_p(x.data_ptr()),
-                                               ctypes.c_void_p(baseline.data_ptr()), B, cptr, K,
-                                               ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(err.data_ptr()),
-                                               _stream_ptr(stream)), "tt_fsi_masked_game_tc")
+    n_bg = 1 if baseline.dim() == 1 else baseline.shape[0]
+    if baseline.shape[-1] != dm.d:
+        raise ValueError("baseline rows must have d entries")
+    _check(native.load().tt_fsi_masked_game_tc_interventional(
+        ctypes.byref(dm.struct), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(baseline.data_ptr()), n_bg, B,
+        cptr, K, ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(err.data_ptr()), _stream_ptr(stream)),
+        "tt_fsi_masked_game_tc_interventional")
     if int(err.item()) != 0:
         raise FsiError(5, "tt_fsi_masked_game_tc")
+    return out
+
+
+def masked_game_interventional(mlp, x, background, dtype=None, stream=None):
+    """Interventional value function (the mean of f over the rows of
+    ``background`` [n, d] for the absent features) for all 2^d coalitions,
+    [B, 2^d] float64 (or float32) by the CUDA kernel."""
+    import torch
+    dm = mlp if isinstance(mlp, DeviceMLP) else DeviceMLP(mlp)
+    dev = dm.W1.device
+    x = torch.as_tensor(x).to(device=dev, dtype=torch.float64).contiguous()
+    if x.dim() == 1:
+        x = x.unsqueeze(0)
+    bg = torch.as_tensor(background).to(device=dev, dtype=torch.float64).contiguous()
+    if bg.dim() != 2 or bg.shape[1] != dm.d:
+        raise ValueError("background must be [n, d]")
+    B = x.shape[0]
+    dt = dtype or torch.float64
+    out = torch.empty((B, 1 << dm.d), dtype=dt, device=dev)
+    _check(native.load().tt_fsi_masked_game_interventional(
+        ctypes.byref(dm.struct), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(bg.data_ptr()), bg.shape[0], B,
+        ctypes.c_void_p(out.data_ptr()), 1 if dt == torch.float32 else 0, _stream_ptr(stream)),
+        "tt_fsi_masked_game_interventional")
     return out
 
 

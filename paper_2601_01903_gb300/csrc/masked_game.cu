@@ -10,7 +10,10 @@
 // coalition (doubling over the G low bits).  Layer 2 is a [2^G, h1] x
 // [h1, h2] product from shared memory, layer 3 a dot product reduced across
 // the two threads that share a coalition.  The float64 instantiation is the
-// parity path; the float32 one generates training labels faster.
+// parity path; the float32 one generates training labels faster.  The
+// interventional value function of Section 4.1 (the mean of f over
+// background rows standing in for the absent features) runs as one launch
+// per background row, each adding f / K to v in ascending row order.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -43,6 +46,8 @@ struct Args {
     int d, h1, h2;
     long long game0;
     const float *W1f, *b1f, *W2f, *b2f, *W3f;
+    double scale;    // v = scale * f (1 for the baseline value function, 1/K per background row)
+    int accumulate;  // add to v instead of overwriting it
 };
 
 // Weights in the arithmetic of the instantiation (float64 or float32 copies).
@@ -110,15 +115,43 @@ __global__ void __launch_bounds__(THREADS) masked_game_kernel(Args a) {
     __syncthreads();
     if (tid < NC && tid < nc) {
         const T val = part[tid] + part[tid + NC] + (T)a.b3;
-        reinterpret_cast<T *>(a.v)[(game << a.d) + S_high + tid] = val;
+        T *out = reinterpret_cast<T *>(a.v) + (game << a.d) + S_high + tid;
+        if (a.accumulate)
+            *out += (T)a.scale * val;
+        else
+            *out = (a.scale == 1.0) ? val : (T)a.scale * val;
     }
 }
 
 }  // namespace ttfsi_mg
 
+namespace ttfsi_mg {
+tt_fsi_status masked_game_launch(const tt_fsi_mlp *model, const double *x_dev, const double *baseline_dev, int64_t B,
+                                 void *v_dev, int out_f32, double scale, int accumulate, struct CUstream_st *stream);
+}  // namespace ttfsi_mg
+
 extern "C" tt_fsi_status tt_fsi_masked_game(const tt_fsi_mlp *model, const double *x_dev,
                                            const double *baseline_dev, int64_t B, void *v_dev,
                                            int out_f32, struct CUstream_st *stream) {
+    return ttfsi_mg::masked_game_launch(model, x_dev, baseline_dev, B, v_dev, out_f32, 1.0, 0, stream);
+}
+
+extern "C" tt_fsi_status tt_fsi_masked_game_interventional(const tt_fsi_mlp *model, const double *x_dev,
+                                                          const double *background_dev, int n_background, int64_t B,
+                                                          void *v_dev, int out_f32, struct CUstream_st *stream) {
+    if (!model || n_background < 1 || !background_dev) return TT_FSI_ERR_INVALID_ARG;
+    const double scale = 1.0 / (double)n_background;
+    for (int k = 0; k < n_background; ++k) {
+        const tt_fsi_status s = ttfsi_mg::masked_game_launch(model, x_dev, background_dev + (size_t)k * model->d, B,
+                                                             v_dev, out_f32, scale, k > 0, stream);
+        if (s != TT_FSI_OK) return s;
+    }
+    return TT_FSI_OK;
+}
+
+tt_fsi_status ttfsi_mg::masked_game_launch(const tt_fsi_mlp *model, const double *x_dev, const double *baseline_dev,
+                                           int64_t B, void *v_dev, int out_f32, double scale, int accumulate,
+                                           struct CUstream_st *stream) {
     using namespace ttfsi_mg;
     if (!model || B < 0) return TT_FSI_ERR_INVALID_ARG;
     if (B == 0) return TT_FSI_OK;
@@ -131,7 +164,7 @@ extern "C" tt_fsi_status tt_fsi_masked_game(const tt_fsi_mlp *model, const doubl
     if (out_f32 && (!model->W2f || !model->b2f || !model->W3f)) return TT_FSI_ERR_INVALID_ARG;
     Args a{model->W1, model->b1, model->W2, model->b2, model->W3, model->b3,
            x_dev, baseline_dev, v_dev, model->d, model->h1, model->h2, 0,
-           model->W1f, model->b1f, model->W2f, model->b2f, model->W3f};
+           model->W1f, model->b1f, model->W2f, model->b2f, model->W3f, scale, accumulate};
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int g = model->d < G ? model->d : G;
     const size_t elem = out_f32 ? sizeof(float) : sizeof(double);
@@ -218,7 +251,7 @@ extern "C" tt_fsi_status tt_fsi_masked_game_sampled(const tt_fsi_mlp *model, con
     if (!model->W1f || !model->b1f || !model->W2f || !model->b2f || !model->W3f) return TT_FSI_ERR_INVALID_ARG;
     Args a{model->W1, model->b1, model->W2, model->b2, model->W3, model->b3,
            x_dev, baseline_dev, nullptr, model->d, model->h1, model->h2, 0,
-           model->W1f, model->b1f, model->W2f, model->b2f, model->W3f};
+           model->W1f, model->b1f, model->W2f, model->b2f, model->W3f, 1.0, 0};
     const long long total = B * (long long)K;
     long long blocks = (total + SW - 1) / SW;
     if (blocks > 65535LL * 16) blocks = 65535LL * 16;

@@ -18,8 +18,12 @@
 //   layer 3 (epilogue): warps w and w + 4 read accumulator rows 32w..32w+31
 //     (their TMEM lane quarter), columns 0-63 and 64-127, with tcgen05.ld and
 //     form b3 + sum_n W3[n] GELU(acc[n] + b2[n]) in FP32.
-// The BF16 rounding of the layer-2 operands is this path's precision (the
-// float64 kernel in masked_game.cu is the parity path).
+// The interventional value function of Section 4.1 (the mean of f over
+// background rows standing in for the absent features) repeats the three
+// layers per background row on the same tile and averages in FP32; one row
+// is the baseline value function.  The BF16 rounding of the layer-2 operands
+// is this path's precision (the float64 kernel in masked_game.cu is the
+// parity path).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -51,7 +55,8 @@ constexpr int kErrTimeout = 1;
 struct Args {
     const float *W1, *b1, *W2, *b2, *W3;
     float b3;
-    const double *x, *base;
+    const double *x, *base;  // base: n_bg background rows [n_bg, d] (one row: the baseline)
+    int n_bg;
     int d;
     long long B;
     const unsigned *coal;  // list mode when non-null: rows are (instance r / K, coal[r])
@@ -93,7 +98,6 @@ __global__ void __launch_bounds__(THREADS) masked_game_tc_kernel(Args a) {
     unsigned char *aA = wB + OPERAND_BYTES;      // activations as the A operand [row][k]
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base_sh;
-    __shared__ int s_fail;
     __shared__ float zrow[ROWS][33];             // list mode: each row's input vector
     __shared__ float sb2[H], sw3[H];
     __shared__ float sdelta[5][H];               // dense mode: w1[k][q] (x_q - baseline_q)
@@ -112,7 +116,6 @@ __global__ void __launch_bounds__(THREADS) masked_game_tc_kernel(Args a) {
     if (tid == 0) {
         mbar_init(smem_u32(&mbar), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_fail = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
@@ -134,7 +137,12 @@ __global__ void __launch_bounds__(THREADS) masked_game_tc_kernel(Args a) {
     const long long tiles_per_inst = a.coal ? 0 : (1ll << (a.d - 7));
     uint32_t parity = 0;
 
-    for (long long t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+    bool failed = false;
+    for (long long t = blockIdx.x; t < a.n_tiles && !failed; t += gridDim.x) {
+      // one pass per background row; each adds its partial layer-3 sums
+      float vsum = 0.f;
+      for (int bgi = 0; bgi < a.n_bg; ++bgi) {
+        const double *base = a.base + (long long)bgi * a.d;
         // ---- layer 1 into the A operand ----
         if (!a.coal) {
             // thread (unit pair kp, quarter qr of the rows): units 2kp, 2kp + 1,
@@ -147,7 +155,7 @@ __global__ void __launch_bounds__(THREADS) masked_game_tc_kernel(Args a) {
             const unsigned cb = c0 | ((unsigned)qr << 5);
             float p0 = a.b1[k0], p1 = a.b1[k0 + 1];
             for (int i = 0; i < a.d; ++i) {
-                const float xi = (float)x[i], bi = (float)a.base[i];
+                const float xi = (float)x[i], bi = (float)base[i];
                 const float wa = __ldg(a.W1 + k0 * a.d + i), wb = __ldg(a.W1 + (k0 + 1) * a.d + i);
                 if (i < 5 && qr == 0) {
                     sdelta[i][k0] = wa * (xi - bi);
@@ -186,7 +194,7 @@ __global__ void __launch_bounds__(THREADS) masked_game_tc_kernel(Args a) {
                     const long long inst = row / a.K;
                     const unsigned m = a.coal[row];
                     const double *x = a.x + inst * a.d;
-                    for (int i = 0; i < a.d; ++i) zrow[tid][i] = (float)(((m >> i) & 1u) ? x[i] : a.base[i]);
+                    for (int i = 0; i < a.d; ++i) zrow[tid][i] = (float)(((m >> i) & 1u) ? x[i] : base[i]);
                 } else {
                     for (int i = 0; i < a.d; ++i) zrow[tid][i] = 0.f;
                 }
@@ -218,7 +226,7 @@ __global__ void __launch_bounds__(THREADS) masked_game_tc_kernel(Args a) {
         const bool ok = mbar_wait(smem_u32(&mbar), parity);
         parity ^= 1u;
         if (__syncthreads_or(ok ? 0 : 1)) {
-            if (tid == 0) s_fail = 1;
+            failed = true;
             break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -240,15 +248,19 @@ __global__ void __launch_bounds__(THREADS) masked_game_tc_kernel(Args a) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) v += sw3[c0 + j] * gelu(__uint_as_float(r[j]) + sb2[c0 + j]);
         }
-        if (warp >= 4) spart[32 * quarter + lane] = v;
-        __syncthreads();
-        const long long row = t * ROWS + 32 * quarter + lane;
-        if (warp < 4 && row < a.n_rows) a.out[row] = a.b3 + v + spart[32 * quarter + lane];
-        // the accumulators and the A operand are rewritten by the next tile
+        vsum += v;
+        // the accumulators and the A operand are rewritten by the next pass
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+      }
+      if (failed) break;
+      const int quarter = warp & 3;
+      if (warp >= 4) spart[32 * quarter + lane] = vsum;
+      __syncthreads();
+      const long long row = t * ROWS + 32 * quarter + lane;
+      if (warp < 4 && row < a.n_rows) a.out[row] = a.b3 + (vsum + spart[32 * quarter + lane]) / (float)a.n_bg;
+      __syncthreads();
     }
-    if (s_fail && tid == 0) atomicOr(a.err, kErrTimeout);
+    if (failed && tid == 0) atomicOr(a.err, kErrTimeout);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(H));
@@ -256,11 +268,26 @@ __global__ void __launch_bounds__(THREADS) masked_game_tc_kernel(Args a) {
 
 }  // namespace ttfsi_mgtc
 
+extern "C" tt_fsi_status tt_fsi_masked_game_tc_interventional(const tt_fsi_mlp *model, const double *x_dev,
+                                                             const double *background_dev, int n_background,
+                                                             int64_t B, const unsigned *coal_dev, int K,
+                                                             float *out_dev, int *err_dev, struct CUstream_st *stream);
+
 extern "C" tt_fsi_status tt_fsi_masked_game_tc(const tt_fsi_mlp *model, const double *x_dev,
                                               const double *baseline_dev, int64_t B, const unsigned *coal_dev,
                                               int K, float *out_dev, int *err_dev, struct CUstream_st *stream) {
+    // a baseline is the interventional value function with one background row
+    return tt_fsi_masked_game_tc_interventional(model, x_dev, baseline_dev, 1, B, coal_dev, K, out_dev, err_dev,
+                                                stream);
+}
+
+extern "C" tt_fsi_status tt_fsi_masked_game_tc_interventional(const tt_fsi_mlp *model, const double *x_dev,
+                                                             const double *background_dev, int n_background,
+                                                             int64_t B, const unsigned *coal_dev, int K,
+                                                             float *out_dev, int *err_dev, struct CUstream_st *stream) {
     using namespace ttfsi_mgtc;
-    if (!model || B < 0) return TT_FSI_ERR_INVALID_ARG;
+    const double *baseline_dev = background_dev;
+    if (!model || B < 0 || n_background < 1) return TT_FSI_ERR_INVALID_ARG;
     if (B == 0) return TT_FSI_OK;
     if (!x_dev || !baseline_dev || !out_dev || !err_dev) return TT_FSI_ERR_INVALID_ARG;
     if (!model->W1f || !model->b1f || !model->W2f || !model->b2f || !model->W3f) return TT_FSI_ERR_INVALID_ARG;
@@ -279,6 +306,7 @@ extern "C" tt_fsi_status tt_fsi_masked_game_tc(const tt_fsi_mlp *model, const do
     a.b3 = (float)model->b3;
     a.x = x_dev;
     a.base = baseline_dev;
+    a.n_bg = n_background;
     a.d = model->d;
     a.B = B;
     a.coal = coal_dev;

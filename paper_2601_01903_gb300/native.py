@@ -143,6 +143,10 @@ def _declare(lib):
     lib.tt_fsi_masked_game.argtypes = [vp, vp, vp, i64, vp, i, vp]
     lib.tt_fsi_masked_game_tc.restype = i
     lib.tt_fsi_masked_game_tc.argtypes = [vp, vp, vp, i64, vp, i, vp, vp, vp]
+    lib.tt_fsi_masked_game_tc_interventional.restype = i
+    lib.tt_fsi_masked_game_tc_interventional.argtypes = [vp, vp, vp, i, i64, vp, i, vp, vp, vp]
+    lib.tt_fsi_masked_game_interventional.restype = i
+    lib.tt_fsi_masked_game_interventional.argtypes = [vp, vp, vp, i, i64, vp, i, vp]
     lib.tt_fsi_apply_noalloc.restype = i
     lib.tt_fsi_apply_noalloc.argtypes = [i, i, vp, i64, vp, vp]
     for name in ("tt_fsi_batch_apply", "tt_fsi_batch_apply_per_game", "tt_fsi_batch_apply_graph"):

@@ -128,3 +128,49 @@ def test_tensor_core_path_rejects_other_shapes():
     with pytest.raises(fsi.FsiError) as e:
         fsi.masked_game_tc(small, synthetic.gaussian_instances(1, 5, seed=1), np.zeros(5))
     assert e.value.status == 2
+
+
+# ---------------------------------------------------------------------------
+# Interventional value function (mean over background rows, Section 4.1)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d,h,B,n_bg", [(9, 16, 2, 5), (14, 32, 1, 3)])
+def test_interventional_float64(oracle_mod, d, h, B, n_bg):
+    mlp = synthetic.random_mlp(d, h, h, seed=d + 50)
+    mlp.b2[:] = 0.1
+    x = synthetic.gaussian_instances(B, d, seed=d)
+    bg = synthetic.gaussian_instances(n_bg, d, seed=d + 1)
+    got = fsi.masked_game_interventional(mlp, x, bg).cpu().numpy()
+    for b in range(B):
+        assert _rel(got[b], oracle_mod.masked_game_interventional(mlp, x[b], bg)) <= TOL
+
+
+@pytest.mark.parametrize("d,B,n_bg", [(12, 2, 4), (16, 1, 3)])
+def test_interventional_tensor_core(oracle_mod, d, B, n_bg):
+    mlp = synthetic.random_mlp(d, 128, 128, seed=60 + d)
+    x = synthetic.gaussian_instances(B, d, seed=d)
+    bg = synthetic.gaussian_instances(n_bg, d, seed=d + 2) * 0.5
+    got = fsi.masked_game_tc(mlp, x, bg).cpu().numpy().astype(np.float64)
+    masks = np.arange(1 << d, dtype=np.int64)
+    for b in range(B):
+        ref = np.mean([_forward_bf16(mlp, _inputs(x[b], bg[k], masks, d)) for k in range(n_bg)], axis=0)
+        assert _rel(got[b], ref) <= TC_EMU_TOL
+        assert _rel(got[b], oracle_mod.masked_game_interventional(mlp, x[b], bg)) <= TC_EXACT_TOL
+    # listed coalitions give the same numbers as the dense tiles
+    coal = synthetic.Stream(d, 3).integers(0, (1 << d) - 1, B * 64).astype(np.uint32).reshape(B, 64)
+    listed = fsi.masked_game_tc(mlp, x, bg, coalitions=coal).cpu().numpy().astype(np.float64)
+    for b in range(B):
+        assert _rel(listed[b], got[b][coal[b].astype(np.int64)]) <= TC_EMU_TOL
+
+
+def test_one_background_row_is_the_baseline_path():
+    d = 13
+    mlp = synthetic.random_mlp(d, 128, 128, seed=2)
+    x = synthetic.gaussian_instances(2, d, seed=2)
+    base = synthetic.gaussian_instances(1, d, seed=9)
+    a = fsi.masked_game_tc(mlp, x, base[0])
+    b = fsi.masked_game_tc(mlp, x, base)
+    assert torch.equal(a, b)
+    c = fsi.masked_game(mlp, x, base[0])
+    e = fsi.masked_game_interventional(mlp, x, base)
+    assert torch.equal(c, e)

@@ -332,3 +332,39 @@ def test_masked_game_end_points_and_null_feature(oracle_mod):
         assert v[S | 4] == v[S & ~4]
     sub = oracle_mod.masked_game(mlp, x, base, coalitions=[0, (1 << d) - 1, 5])
     assert np.array_equal(sub, v[[0, (1 << d) - 1, 5]])
+
+
+# ---------------------------------------------------------------------------
+# Interventional value function (Section 4.1): pinned by direct forward passes
+# ---------------------------------------------------------------------------
+
+def _mlp_forward(mlp, z):
+    """f(z) written out for a batch of inputs (GELU in the erf form)."""
+    from math import erf, sqrt
+    g = np.vectorize(lambda t: 0.5 * t * (1.0 + erf(t / sqrt(2.0))))
+    a1 = g(z @ np.asarray(mlp.W1).T + mlp.b1)
+    a2 = g(a1 @ np.asarray(mlp.W2).T + mlp.b2)
+    return a2 @ np.asarray(mlp.W3).reshape(-1) + float(np.asarray(mlp.b3).reshape(-1)[0])
+
+
+def test_interventional_value_function_end_points_and_rows(oracle_mod):
+    from paper_2601_01903_gb300 import synthetic
+    d = 7
+    mlp = synthetic.random_mlp(d, 12, 9, seed=3)
+    mlp.b1[:] = 0.2
+    x = synthetic.gaussian_instances(1, d, seed=5)[0]
+    bg = synthetic.gaussian_instances(4, d, seed=6)
+    v = oracle_mod.masked_game_interventional(mlp, x, bg)
+    # all features present: the background does not matter
+    assert abs(v[(1 << d) - 1] - _mlp_forward(mlp, x[None, :])[0]) < 1e-12
+    # no feature present: the mean prediction over the background rows
+    assert abs(v[0] - _mlp_forward(mlp, bg).mean()) < 1e-12
+    # coalition {0, 3}: the mean over rows of f with x_0, x_3 put in
+    z = bg.copy()
+    z[:, [0, 3]] = x[[0, 3]]
+    assert abs(v[0b1001] - _mlp_forward(mlp, z).mean()) < 1e-12
+    # one row is the baseline value function; repeating a row changes nothing
+    assert np.allclose(oracle_mod.masked_game_interventional(mlp, x, bg[1:2]), oracle_mod.masked_game(mlp, x, bg[1]),
+                       rtol=0, atol=1e-14)
+    assert np.allclose(oracle_mod.masked_game_interventional(mlp, x, np.repeat(bg[2:3], 3, axis=0)),
+                       oracle_mod.masked_game(mlp, x, bg[2]), rtol=0, atol=1e-13)
