@@ -44,13 +44,15 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--epochs", type=int, default=200, help="student mode: training epochs")
     ap.add_argument("--workload", default="mlp_d20_l3_b16",
-                    choices=["mlp_d20_l3_b16", "uneven_1024", "student", "configs", "value_function"],
+                    choices=["mlp_d20_l3_b16", "uneven_1024", "student", "student_step", "configs",
+                             "value_function"],
                     help="mlp_d20_l3_b16: the headline batch; uneven_1024: 1024 Moebius-sparse "
                          "games with d in 10..20 and l in 1..3, one persistent launch vs "
                          "per-game launches vs a CUDA graph of them; student: the amortised "
                          "explainer; configs: device time of every single-plan configuration "
                          "(each arithmetic, order 4, the other indices), one JSON line; "
-                         "value_function: the masked-model value function on each path")
+                         "value_function: the masked-model value function on each path; "
+                         "student_step: the explainer's training step alone (synthetic batch)")
     return ap.parse_args()
 
 
@@ -420,6 +422,45 @@ def run_configs(args, rank, world, local_rank):
                           "n_gpus": 1, "data": "synthetic", "rows": rows}), flush=True)
 
 
+def run_student_step(args, rank, world, local_rank):
+    """The amortised explainer's training step alone: student 16-1024-1024-137,
+    batch 4096, synthetic inputs and labels (the step's arithmetic does not
+    depend on the values), --steps timed steps after --warmup."""
+    import torch
+    from paper_2601_01903_gb300 import student as st, synthetic
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    d, H, n_out, B = 16, 1024, 137, 4096
+    s = st.Student(d, H, n_out, B, st.init_params(d, H, n_out, 4))
+    g = synthetic.Stream(4, 77)
+    x = torch.as_tensor(g.normal(B * d).reshape(B, d), dtype=torch.float32, device=dev)
+    lab = torch.as_tensor(g.normal(B * n_out).reshape(B, n_out) * 0.01, dtype=torch.float32, device=dev)
+    tgt = torch.as_tensor(g.normal(B), dtype=torch.float32, device=dev)
+    for _ in range(max(3, args.warmup)):
+        s.train_step(x, lab, tgt, 0.0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clocks:
+        e0.record()
+        for _ in range(args.steps):
+            s.train_step(x, lab, tgt, 0.0)
+        e1.record()
+        torch.cuda.synchronize()
+    s.check()
+    ms = e0.elapsed_time(e1) / args.steps
+    flop = 3 * 2 * B * (d * H + H * H + H * n_out)
+    mb = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops_sustained": 1700.0}
+    peak = float(mb.get("bf16_tflops_sustained", 1700.0))
+    if rank == 0:
+        print(json.dumps({"metric": "student training step (forward, backward, Adam) on tcgen05", "value": ms,
+                          "unit": "ms/step", "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
+                          "data": "synthetic", "config": {"workload": "student_step", "d": d, "hidden": H,
+                                                          "n_out": n_out, "batch": B},
+                          "tflops": flop / (ms * 1e-3) / 1e12, "frac_of_sustained_bf16": flop / (ms * 1e-3) / 1e12 / peak,
+                          "clocks": clocks.summary()}), flush=True)
+
+
 def run_value_function(args, rank, world, local_rank):
     """Device time of the value function v_x(S) for every coalition: float64
     and float32 CUDA-core kernels, the tensor-core kernel, and the
@@ -639,6 +680,8 @@ def main():
             run_configs(args, rank, world, local_rank)
         elif args.workload == "value_function":
             run_value_function(args, rank, world, local_rank)
+        elif args.workload == "student_step":
+            run_student_step(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

@@ -323,7 +323,10 @@ extern "C" tt_fsi_status tt_fsi_masked_game_tc_interventional(const tt_fsi_mlp *
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, masked_game_tc_kernel, THREADS, SMEM_BYTES);
     if (e != cudaSuccess) return TT_FSI_ERR_CUDA;
-    const long long grid = std::min<long long>(a.n_tiles, (long long)std::max(1, occ) * sms);
+    // two CTAs per SM fit (shared memory and registers); a persistent grid of
+    // at least that many keeps one CTA's CUDA-core layers beside the other's
+    // tensor-core wait
+    const long long grid = std::min<long long>(a.n_tiles, (long long)std::max(2, occ) * sms);
     masked_game_tc_kernel<<<(unsigned)grid, THREADS, SMEM_BYTES, reinterpret_cast<cudaStream_t>(stream)>>>(a);
     return cudaGetLastError() == cudaSuccess ? TT_FSI_OK : TT_FSI_ERR_CUDA;
 }
