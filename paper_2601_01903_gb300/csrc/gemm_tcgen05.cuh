@@ -1,5 +1,7 @@
 // BF16 x BF16 -> FP32 GEMM on the 5th-generation tensor cores of sm_103a
-// (tcgen05.mma, accumulators in tensor memory), with fused epilogues.
+// (tcgen05.mma, accumulators in tensor memory), with fused epilogues, in
+// two forms: operands fed by the Tensor Memory Accelerator (the default,
+// below) or by cp.async (used where an operand has no tensor map).
 //
 //   C[M, N] = A[M, K] . B[N, K]^T      (both operands K-major, row-major in HBM)
 //
@@ -17,6 +19,7 @@
 // writing FP32 and/or BF16 outputs, optionally also transposed.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -161,6 +164,82 @@ __device__ __forceinline__ void load_tile(uint32_t tile, const __nv_bfloat16 *G,
 }
 
 #ifndef TTFSI_GEMM_HELPERS_ONLY
+// Epilogue of one 128 x BN tile from its TMEM accumulators (see the header).
+// `stage_all` is idle shared memory, 32 x 33 floats per warp; `slot` picks
+// the warp's block, the warp reads TMEM lane quarter `quarter` (tile rows
+// 32 quarter ..) over accumulator columns [cb, ce).
+__device__ __forceinline__ void gemm_epilogue(const GemmArgs &a, float *Cf, uint32_t tmem, float *stage_all, int m0,
+                                              int n0, int slot, int quarter, int cb, int ce, int lane) {
+        float *stage = stage_all + slot * (32 * 33);
+        // Epilogue, 32 columns at a time.  Warp w owns accumulator rows
+        // 32w..32w+31 (its TMEM lane quarter); tcgen05.ld gives each lane one
+        // row, so the values go through a per-warp 32 x 33 staging block in
+        // the (now idle) operand tiles and leave with lanes over columns
+        // (row-major outputs) or over rows (the transposed output), i.e. as
+        // coalesced stores.
+        const int rbase = m0 + 32 * quarter;
+        for (int c0 = cb; c0 < ce; c0 += 32) {
+            uint32_t r[32];
+            const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr));
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+                  "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                  "=r"(r[30]), "=r"(r[31])
+                : "r"(taddr + 16u));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(r[j]);
+            __syncwarp();
+            // row pass: lane = column; the pre-activations of the GELU factor
+            // are loaded 8 rows at a time ahead of their use, so the loads overlap
+            const int col = n0 + c0 + lane;
+            const bool col_ok = col < a.N;
+            const float bias = (a.bias && col_ok) ? a.bias[col] : 0.f;
+#pragma unroll 1
+            for (int i0 = 0; i0 < 32; i0 += 8) {
+                float zin[8];
+                if (a.dgelu_z) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        zin[i] = (col_ok && rbase + i0 + i < a.M) ? a.dgelu_z[(long long)(rbase + i0 + i) * a.ldz + col]
+                                                                  : 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int row = rbase + i0 + i;
+                    if (row < a.M && col_ok) {
+                        float z = stage[(i0 + i) * 33 + lane] + bias;
+                        if (a.dgelu_z) z *= gelu_grad_f(zin[i]);
+                        if (Cf) Cf[(long long)row * a.ldcf + col] = z;
+                        const float y = (a.act == 1) ? gelu_f(z) : z;
+                        if (a.Cb) a.Cb[(long long)row * a.ldcb + col] = __float2bfloat16_rn(y);
+                        stage[(i0 + i) * 33 + lane] = y;
+                    }
+                }
+            }
+            if (a.Ct) {
+                __syncwarp();
+                // column pass: lane = row
+                const int row = rbase + lane;
+                if (row < a.M)
+                    for (int j = 0; j < 32; ++j) {
+                        const int colj = n0 + c0 + j;
+                        if (colj < a.N) a.Ct[(long long)colj * a.ldct + row] = __float2bfloat16_rn(stage[lane * 33 + j]);
+                    }
+            }
+            __syncwarp();
+        }
+}
+
 __global__ void __launch_bounds__(THREADS) gemm_bf16_tcgen05(GemmArgs a) {
     extern __shared__ __align__(1024) unsigned char gsm_raw[];
     // 1024-byte alignment of the operand tiles (the swizzle is address based)
@@ -249,74 +328,129 @@ __global__ void __launch_bounds__(THREADS) gemm_bf16_tcgen05(GemmArgs a) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
     if (!s_fail) {
-        // Epilogue, 32 columns at a time.  Warp w owns accumulator rows
-        // 32w..32w+31 (its TMEM lane quarter); tcgen05.ld gives each lane one
-        // row, so the values go through a per-warp 32 x 33 staging block in
-        // the (now idle) operand tiles and leave with lanes over columns
-        // (row-major outputs) or over rows (the transposed output), i.e. as
-        // coalesced stores.
-        float *stage = reinterpret_cast<float *>(gsm_raw + (base - raw)) + warp * (32 * 33);
-        const int rbase = m0 + 32 * warp;
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-            uint32_t r[32];
-            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                "[%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15])
-                : "r"(taddr));
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                "[%16];"
-                : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
-                  "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-                  "=r"(r[30]), "=r"(r[31])
-                : "r"(taddr + 16u));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-            for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(r[j]);
-            __syncwarp();
-            // row pass: lane = column; the pre-activations of the GELU factor
-            // are loaded 8 rows at a time ahead of their use, so the loads overlap
-            const int col = n0 + c0 + lane;
-            const bool col_ok = col < a.N;
-            const float bias = (a.bias && col_ok) ? a.bias[col] : 0.f;
-#pragma unroll 1
-            for (int i0 = 0; i0 < 32; i0 += 8) {
-                float zin[8];
-                if (a.dgelu_z) {
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        zin[i] = (col_ok && rbase + i0 + i < a.M) ? a.dgelu_z[(long long)(rbase + i0 + i) * a.ldz + col]
-                                                                  : 0.f;
-                }
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int row = rbase + i0 + i;
-                    if (row < a.M && col_ok) {
-                        float z = stage[(i0 + i) * 33 + lane] + bias;
-                        if (a.dgelu_z) z *= gelu_grad_f(zin[i]);
-                        if (Cf) Cf[(long long)row * a.ldcf + col] = z;
-                        const float y = (a.act == 1) ? gelu_f(z) : z;
-                        if (a.Cb) a.Cb[(long long)row * a.ldcb + col] = __float2bfloat16_rn(y);
-                        stage[(i0 + i) * 33 + lane] = y;
-                    }
-                }
-            }
-            if (a.Ct) {
-                __syncwarp();
-                // column pass: lane = row
-                const int row = rbase + lane;
-                if (row < a.M)
-                    for (int j = 0; j < 32; ++j) {
-                        const int colj = n0 + c0 + j;
-                        if (colj < a.N) a.Ct[(long long)colj * a.ldct + row] = __float2bfloat16_rn(stage[lane * 33 + j]);
-                    }
-            }
-            __syncwarp();
+        gemm_epilogue(a, Cf, tmem, reinterpret_cast<float *>(gsm_raw + (base - raw)), m0, n0, warp, warp, 0, BN, lane);
+    } else if (threadIdx.x == 0) {
+        atomicOr(a.err, kErrGemmTimeout);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+}
+
+// ----------------------------------------------------------------------------
+// The same product with the operands fed by the Tensor Memory Accelerator:
+// one thread (warp 0) issues 2D tiled bulk-tensor loads of the 128 x 64
+// operand tiles, 128-byte swizzled by the copy engine into the layout the
+// MMA descriptors describe, into TMA_STAGES stages; each stage has a "full"
+// mbarrier (the loads' transaction bytes) and an "empty" one (the MMAs that
+// read it, via tcgen05.commit).  One thread (warp 1) waits on "full" and
+// issues the MMAs; all 8 warps then run the epilogue once a final commit
+// signals that the accumulator is complete (two warps per TMEM lane
+// quarter, one per half of the columns).  Rows, columns and K beyond the
+// operands are zero-filled by the loads.  Every wait is bounded; a wait that
+// runs out records kErrGemmTimeout and the CTA skips its epilogue.
+// ----------------------------------------------------------------------------
+constexpr int TMA_STAGES = 2;     // 66.5 KB: three CTAs per SM
+constexpr int TMA_THREADS = 256;  // 8 warps for the epilogue
+constexpr int TMA_SMEM_BYTES = TMA_STAGES * 2 * TILE_BYTES + 1024;
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(tmap), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__global__ void __launch_bounds__(TMA_THREADS) gemm_bf16_tcgen05_tma(const __grid_constant__ GemmArgs a,
+                                                                 const __grid_constant__ CUtensorMap tmA,
+                                                                 const __grid_constant__ CUtensorMap tmB) {
+    extern __shared__ __align__(1024) unsigned char gsm_raw[];
+    const uint32_t raw = smem_u32(gsm_raw);
+    const uint32_t base = (raw + 1023) & ~1023u;
+    __shared__ __align__(8) uint64_t full[TMA_STAGES], empty[TMA_STAGES], done;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int s_fail;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int nk_all = (a.K + BK - 1) / BK;
+    const int kb0 = a.kbc > 0 ? (int)blockIdx.z * a.kbc : 0;
+    const int nk = a.kbc > 0 ? min(a.kbc, nk_all - kb0) : nk_all;
+    float *const Cf = a.Cf ? a.Cf + (long long)blockIdx.z * a.cf_zstride : nullptr;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TMA_STAGES; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
         }
+        mbar_init(smem_u32(&done), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+
+    auto tileA = [&](int s) { return base + (uint32_t)(s * 2) * TILE_BYTES; };
+    auto tileB = [&](int s) { return base + (uint32_t)(s * 2 + 1) * TILE_BYTES; };
+
+    if (threadIdx.x == 0) {
+        // producer
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % TMA_STAGES;
+            const uint32_t use = (uint32_t)(kb / TMA_STAGES);
+            if (use > 0 && !mbar_wait(smem_u32(&empty[s]), (use - 1) & 1u)) {
+                atomicOr(&s_fail, 1);
+                break;
+            }
+            if (*(volatile int *)&s_fail) break;
+            mbar_expect_tx(smem_u32(&full[s]), 2u * TILE_BYTES);
+            const int k0 = (kb0 + kb) * BK;
+            tma_load_2d(tileA(s), &tmA, k0, m0, smem_u32(&full[s]));
+            tma_load_2d(tileB(s), &tmB, k0, n0, smem_u32(&full[s]));
+        }
+    } else if (threadIdx.x == 32) {
+        // MMA issuer
+        const uint32_t idesc = instr_desc_bf16(BM, BN);
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % TMA_STAGES;
+            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)(kb / TMA_STAGES) & 1u)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int k16 = 0; k16 < BK / 16; ++k16) {
+                const uint64_t da = smem_desc(tileA(s) + k16 * 32);
+                const uint64_t db = smem_desc(tileB(s) + k16 * 32);
+                mma_bf16(tmem, da, db, idesc, (kb > 0 || k16 > 0) ? 1u : 0u);
+            }
+            mma_commit(smem_u32(&empty[s]));
+        }
+        if (!ok) atomicOr(&s_fail, 1);
+        mma_commit(smem_u32(&done));  // arrives once every MMA issued above has completed
+    }
+    // every thread: wait for the accumulator (or the failure flag)
+    const bool ok = mbar_wait(smem_u32(&done), 0);
+    if (!ok) atomicOr(&s_fail, 1);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!s_fail) {
+        // the stage buffers are idle: every load was consumed by an MMA that has completed
+        // 8 warps: warps w and w + 4 share TMEM lane quarter w & 3 and take
+        // the accumulator columns [0, BN/2) and [BN/2, BN)
+        gemm_epilogue(a, Cf, tmem, reinterpret_cast<float *>(gsm_raw + (base - raw)), m0, n0, warp, warp & 3,
+                      (warp >> 2) * (BN / 2), (warp >> 2) * (BN / 2) + BN / 2, lane);
     } else if (threadIdx.x == 0) {
         atomicOr(a.err, kErrGemmTimeout);
     }

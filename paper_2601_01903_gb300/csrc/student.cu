@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 
 #include "gemm_tcgen05.cuh"
@@ -19,6 +21,39 @@ tt_fsi_status st_status(cudaError_t e) {
 
 bool g_gemm_attr_set[64] = {false};
 
+// The driver's tensor-map encoder, looked up through the runtime (so the
+// library does not link the driver library itself); null if unavailable.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// Tensor map of a row-major BF16 operand [rows, K] with row pitch ld
+// elements: 128 x 64 boxes, 128-byte swizzle, zero fill outside the matrix.
+bool operand_tensor_map(CUtensorMap *map, const __nv_bfloat16 *ptr, int rows, int K, int ld) {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(__nv_bfloat16)};
+    const cuuint32_t box[2] = {(cuuint32_t)ttfsi_gemm::BK, (cuuint32_t)ttfsi_gemm::BM};
+    const cuuint32_t estr[2] = {1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(ptr), dims, strides, box,
+                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Launches the TMA-fed kernel, or the cp.async kernel where an operand has
+// no valid tensor map (the two compute the same products).
 tt_fsi_status gemm_launch(const ttfsi_gemm::GemmArgs &a, cudaStream_t st) {
     using namespace ttfsi_gemm;
     if (a.M <= 0 || a.N <= 0 || a.K <= 0) return TT_FSI_OK;
@@ -26,13 +61,20 @@ tt_fsi_status gemm_launch(const ttfsi_gemm::GemmArgs &a, cudaStream_t st) {
     if (cudaGetDevice(&dev) != cudaSuccess) return TT_FSI_ERR_CUDA;
     if (dev >= 0 && dev < 64 && !g_gemm_attr_set[dev]) {
         cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tcgen05, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(gemm_bf16_tcgen05_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     TMA_SMEM_BYTES);
         if (e != cudaSuccess) return st_status(e);
         g_gemm_attr_set[dev] = true;
     }
     const int nk = (a.K + BK - 1) / BK;
     const int kslices = a.kbc > 0 ? (nk + a.kbc - 1) / a.kbc : 1;
     dim3 grid((unsigned)((a.N + BN - 1) / BN), (unsigned)((a.M + BM - 1) / BM), (unsigned)kslices);
-    gemm_bf16_tcgen05<<<grid, THREADS, SMEM_BYTES, st>>>(a);
+    CUtensorMap tmA, tmB;
+    if (operand_tensor_map(&tmA, a.A, a.M, a.K, a.lda) && operand_tensor_map(&tmB, a.B, a.N, a.K, a.ldb))
+        gemm_bf16_tcgen05_tma<<<grid, TMA_THREADS, TMA_SMEM_BYTES, st>>>(a, tmA, tmB);
+    else
+        gemm_bf16_tcgen05<<<grid, THREADS, SMEM_BYTES, st>>>(a);
     return st_status(cudaGetLastError());
 }
 

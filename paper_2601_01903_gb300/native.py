@@ -80,7 +80,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
             objs = list(ex.map(compile_one, srcs))
         tmp = LIB_PATH + f".{os.getpid()}.tmp"
-        cmd = [nvcc(), ARCH, "-shared", "-o", tmp] + objs + ["-lcudart", "-lcuda"]
+        cmd = [nvcc(), ARCH, "-shared", "-o", tmp] + objs + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
