@@ -415,8 +415,34 @@ def run_configs(args, rank, world, local_rank):
                 rows.append({"config": label, "index": index, "arith": arith, "d": d, "ell": ell, "B": B,
                              "ms_per_call": ms, "coalitions_per_s": B * (1 << d) / (ms * 1e-3),
                              "hbm_frac_of_measured": B * (1 << d) * elem / (ms * 1e-3) / 1e9 / peaks()[0],
-                             "calls_timed": reps})
+                             "calls_timed": reps, "variant": "default"})
                 plan.close()
+    # the comparison variant: the same scores by the site-by-site sweep
+    for label, key, d, ell in specs[2:4]:
+        v64 = inputs(key)
+        B = v64.shape[0]
+        for arith in ("exact", "f32"):
+            v = v64.float() if arith == "f32" else v64
+            plan = fsi.Plan(d, ell, arith, max_batch=B, site_sweep=True)
+            out = torch.empty((B, plan.n_scores), dtype=v.dtype, device=dev)
+            for i in range(2):
+                plan.apply(v, out=out)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for i in range(5):
+                plan.apply(v, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            plan.check()
+            ms = e0.elapsed_time(e1) / 5
+            elem = 4 if arith == "f32" else 8
+            rows.append({"config": label, "index": "fsi", "arith": arith, "d": d, "ell": ell, "B": B,
+                         "ms_per_call": ms, "coalitions_per_s": B * (1 << d) / (ms * 1e-3),
+                         "hbm_frac_of_measured": B * (1 << d) * elem / (ms * 1e-3) / 1e9 / peaks()[0],
+                         "calls_timed": 5, "variant": "site-by-site sweep (Algorithm 1 form)",
+                         "tile_bits": plan.tile_bits})
+            plan.close()
     if rank == 0:
         print(json.dumps({"metric": "device time of tt_fsi_apply per configuration", "unit": "coalitions/s",
                           "n_gpus": 1, "data": "synthetic", "rows": rows}), flush=True)

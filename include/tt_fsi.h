@@ -120,6 +120,24 @@ tt_fsi_status tt_fsi_plan_create(int d, int ell, tt_fsi_arith arith, int64_t max
 tt_fsi_status tt_fsi_plan_create_index(int d, int ell, tt_fsi_index index, tt_fsi_arith arith,
                                        int64_t max_batch, tt_fsi_plan *out);
 
+/*
+ * Plan options for tt_fsi_plan_create_ex.
+ *  TT_FSI_PLAN_SITE_SWEEP: contract every tile site by site, one bit per
+ *    step, in the form of the paper's sweep (Section 3.3, Algorithm 1): the
+ *    MPO bond state of an output is its prefix sigma on the processed sites
+ *    and the counter |T \ S| so far, each step applies the site core (at
+ *    most 3 transitions per state, from a table), with the state space
+ *    pruned to |sigma| <= l; the high bits are folded in by the same
+ *    cross-tile combine.  Same scores as the default plan (which runs the
+ *    12-bit tiles in three 4-bit register groups); kept as the comparison
+ *    variant of the paper's own formulation.
+ */
+#define TT_FSI_PLAN_SITE_SWEEP 1u
+
+/* As tt_fsi_plan_create_index, with option flags (0 or TT_FSI_PLAN_*). */
+tt_fsi_status tt_fsi_plan_create_ex(int d, int ell, tt_fsi_index index, tt_fsi_arith arith, int64_t max_batch,
+                                    unsigned flags, tt_fsi_plan *out);
+
 /* Releases a plan and its device memory (synchronizes the device first).
  * Accepts NULL. */
 void tt_fsi_plan_destroy(tt_fsi_plan plan);

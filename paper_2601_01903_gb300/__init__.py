@@ -58,12 +58,15 @@ class Plan:
     """tt_fsi_plan(d, l): tables and scratch for FSI of order ``ell`` on
     ``d``-player games, for batches of up to ``max_batch`` games."""
 
-    def __init__(self, d: int, ell: int, arith: str = "exact", max_batch: int = 1, index: str = "fsi"):
+    def __init__(self, d: int, ell: int, arith: str = "exact", max_batch: int = 1, index: str = "fsi",
+                 site_sweep: bool = False):
+        """site_sweep: contract every tile site by site (the paper's sweep),
+        the comparison variant of the default 4-bit register groups."""
         self._lib = native.load()
         self.d, self.ell, self.arith, self.max_batch, self.index = d, ell, arith, max_batch, index
         h = ctypes.c_void_p()
-        _check(self._lib.tt_fsi_plan_create_index(d, ell, INDEX[index], ARITH[arith], max_batch,
-                                                  ctypes.byref(h)), "tt_fsi_plan_create_index")
+        _check(self._lib.tt_fsi_plan_create_ex(d, ell, INDEX[index], ARITH[arith], max_batch,
+                                               1 if site_sweep else 0, ctypes.byref(h)), "tt_fsi_plan_create_ex")
         self._h = h
         self.n_scores = num_scores(d, ell)
 

@@ -796,12 +796,17 @@ tt_fsi_status tt_fsi_plan_create(int d, int ell, tt_fsi_arith arith, int64_t max
 
 tt_fsi_status tt_fsi_plan_create_index(int d, int ell, tt_fsi_index index, tt_fsi_arith arith,
                                        int64_t max_batch, tt_fsi_plan *out) {
-    if (!out) return TT_FSI_ERR_INVALID_ARG;
+    return tt_fsi_plan_create_ex(d, ell, index, arith, max_batch, 0u, out);
+}
+
+tt_fsi_status tt_fsi_plan_create_ex(int d, int ell, tt_fsi_index index, tt_fsi_arith arith, int64_t max_batch,
+                                    unsigned flags, tt_fsi_plan *out) {
+    if (!out || (flags & ~(unsigned)TT_FSI_PLAN_SITE_SWEEP)) return TT_FSI_ERR_INVALID_ARG;
     *out = nullptr;
     tt_fsi_plan_s *h = new (std::nothrow) tt_fsi_plan_s();
     if (!h) return TT_FSI_ERR_NO_MEMORY;
     Plan &p = h->p;
-    tt_fsi_status st = plan_build_host(p, d, ell, arith, max_batch, index);
+    tt_fsi_status st = plan_build_host(p, d, ell, arith, max_batch, index, (flags & TT_FSI_PLAN_SITE_SWEEP) != 0);
     if (st != TT_FSI_OK) {
         delete h;
         return st;

@@ -106,7 +106,7 @@ struct Plan {
 
 // Builds every host table of the plan (no CUDA calls).  Returns a status.
 tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64_t max_batch,
-                              tt_fsi_index index = TT_FSI_INDEX_FSI);
+                              tt_fsi_index index = TT_FSI_INDEX_FSI, bool site_sweep = false);
 
 // Scores and their order.
 int64_t num_scores(int d, int ell);

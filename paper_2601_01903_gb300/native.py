@@ -112,6 +112,8 @@ def _declare(lib):
     lib.tt_fsi_plan_create.argtypes = [i, i, i, i64, c.POINTER(vp)]
     lib.tt_fsi_plan_create_index.restype = i
     lib.tt_fsi_plan_create_index.argtypes = [i, i, i, i, i64, c.POINTER(vp)]
+    lib.tt_fsi_plan_create_ex.restype = i
+    lib.tt_fsi_plan_create_ex.argtypes = [i, i, i, i, i64, c.c_uint, c.POINTER(vp)]
     lib.tt_fsi_batch_create_index.restype = i
     lib.tt_fsi_batch_create_index.argtypes = [vp, i64, i, i, c.POINTER(vp)]
     lib.tt_fsi_plan_destroy.restype = None

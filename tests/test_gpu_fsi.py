@@ -240,3 +240,15 @@ def test_order_4_float32_error_is_small(oracle_mod):
     v = _noise_games(d, 2, seed=77)
     got, _ = _run(v, d, 4, "f32")
     assert _rel_err(got, oracle_mod.fsi(v, d, 4), v) <= 1e-4
+
+
+@pytest.mark.parametrize("arith", ["exact", "f64"])
+@pytest.mark.parametrize("d,ell,B", [(14, 2, 3), (16, 3, 2), (9, 3, 2), (13, 4, 1)])
+def test_site_sweep_variant_matches_oracle(oracle_mod, arith, d, ell, B):
+    """The site-by-site sweep (comparison variant of the paper's own
+    formulation) gives the same scores within the parity bar."""
+    v = _noise_games(d, B, seed=700 + d + ell)
+    plan = fsi.Plan(d, ell, arith, max_batch=B, site_sweep=True)
+    got = plan.apply(_gpu(v)).cpu().numpy()
+    plan.check()
+    assert _rel_err(got, oracle_mod.fsi(v, d, ell), v) <= TOL
