@@ -312,14 +312,10 @@ def run_ours(args, rank, world, local_rank):
     v_host = copies[0].cpu().pin_memory()
     phi_host = torch.empty(phi.shape, dtype=phi.dtype).pin_memory()
     for _ in range(2):
-        lib.tt_fsi_apply_host(plan.handle, ctypes.c_void_p(v_host.data_ptr()), BATCH,
-                              ctypes.c_void_p(phi_host.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+        plan.apply_host(v_host, out=phi_host, stream=stream)
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        st = lib.tt_fsi_apply_host(plan.handle, ctypes.c_void_p(v_host.data_ptr()), BATCH,
-                                   ctypes.c_void_p(phi_host.data_ptr()),
-                                   ctypes.c_void_p(stream.cuda_stream))
-        assert st == 0, st
+        plan.apply_host(v_host, out=phi_host, stream=stream)
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
     e2e = {"value": world * BATCH * n / e2e_s, "unit": "coalitions/s",
            "h2d_bytes_per_step": BATCH * n * elem, "d2h_bytes_per_step": BATCH * plan.n_scores * elem}

@@ -163,11 +163,20 @@ tt_fsi_status tt_fsi_apply(tt_fsi_plan plan, const void *v_dev, int64_t B, void 
  * v_host [B, 2^d] to a device staging buffer owned by the plan (allocated on
  * the plan's first tt_fsi_apply_host call, max_batch games in size), runs
  * tt_fsi_apply, copies the scores to phi_host [B, n_scores] and waits for the
- * stream before returning.  Page-locked host buffers copy fastest; pageable
- * ones work.  Element types as for tt_fsi_apply.
+ * stream before returning.  The input moves in chunks of whole games on a
+ * copy stream owned by the plan, and each chunk is computed on `stream` as
+ * soon as it has arrived, so transfer and compute overlap (chunk size:
+ * tt_fsi_plan_set_host_chunk).  Results do not depend on the chunking.
+ * Page-locked host buffers copy fastest; pageable ones work.  Element types
+ * as for tt_fsi_apply.  One call at a time per plan.
  */
 tt_fsi_status tt_fsi_apply_host(tt_fsi_plan plan, const void *v_host, int64_t B, void *phi_host,
                                 struct CUstream_st *stream);
+
+/* Games per host-transfer chunk of tt_fsi_apply_host: 0 (the default) picks
+ * chunks of at least 4 MiB and at most 16 per call; games >= 1 fixes it.
+ * TT_FSI_ERR_INVALID_ARG for games < 0. */
+tt_fsi_status tt_fsi_plan_set_host_chunk(tt_fsi_plan plan, int64_t games);
 
 /*
  * Tracing.  tt_fsi_plan_profile(plan, 1) makes every later tt_fsi_apply of

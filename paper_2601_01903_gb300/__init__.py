@@ -111,6 +111,31 @@ class Plan:
                "tt_fsi_apply")
         return out
 
+    def apply_host(self, v, out=None, stream=None):
+        """End to end from host memory: v [B, 2^d] CPU tensor (page-locked
+        copies fastest) -> phi [B, n_scores] CPU tensor; the input moves to
+        the device in chunks that overlap the compute."""
+        import torch
+        dt = torch.float32 if self.arith == "f32" else torch.float64
+        if v.dim() == 1:
+            v = v.unsqueeze(0)
+        if v.is_cuda or v.dtype != dt or v.shape[-1] != (1 << self.d):
+            raise ValueError(f"v must be a CPU {dt} tensor of shape [B, 2^{self.d}]")
+        v = v.contiguous()
+        B = v.shape[0]
+        if out is None:
+            out = torch.empty((B, self.n_scores), dtype=dt, pin_memory=v.is_pinned())
+        if out.is_cuda or out.dtype != dt or tuple(out.shape) != (B, self.n_scores) or not out.is_contiguous():
+            raise ValueError(f"out must be a contiguous CPU {dt} tensor of shape [B, {self.n_scores}]")
+        _check(self._lib.tt_fsi_apply_host(self._h, ctypes.c_void_p(v.data_ptr()), B,
+                                           ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+               "tt_fsi_apply_host")
+        return out
+
+    def set_host_chunk(self, games: int = 0):
+        """Games per host-transfer chunk of apply_host (0: automatic)."""
+        _check(self._lib.tt_fsi_plan_set_host_chunk(self._h, games), "tt_fsi_plan_set_host_chunk")
+
     def check(self, stream=None):
         _check(self._lib.tt_fsi_plan_check(self._h, _stream_ptr(stream)), "tt_fsi_plan_check")
 

@@ -761,9 +761,13 @@ struct tt_fsi_plan_s {
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::array<cudaEvent_t, 3>> ev_rec;
-    // staging for tt_fsi_apply_host
+    // staging for tt_fsi_apply_host: device buffers, the copy stream that
+    // fills them chunk by chunk, and the games per chunk (0: automatic)
     void *d_v_stage = nullptr;
     void *d_phi_stage = nullptr;
+    cudaStream_t s_copy = nullptr;
+    cudaEvent_t ev_copy = nullptr;
+    int64_t host_chunk = 0;
 };
 
 namespace {
@@ -892,6 +896,8 @@ void tt_fsi_plan_destroy(tt_fsi_plan plan) {
     free_plan_device(&plan->p);
     cudaFree(plan->d_v_stage);
     cudaFree(plan->d_phi_stage);
+    if (plan->ev_copy) cudaEventDestroy(plan->ev_copy);
+    if (plan->s_copy) cudaStreamDestroy(plan->s_copy);
     for (auto &r : plan->ev_rec)
         for (cudaEvent_t ev : r) cudaEventDestroy(ev);
     for (cudaEvent_t ev : plan->ev_pool) cudaEventDestroy(ev);
@@ -943,14 +949,52 @@ tt_fsi_status tt_fsi_apply_host(tt_fsi_plan plan, const void *v_host, int64_t B,
             return cuda_status(e);
         }
     }
+    if (!plan->s_copy) {
+        cudaError_t e = cudaStreamCreateWithFlags(&plan->s_copy, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&plan->ev_copy, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            if (plan->s_copy) cudaStreamDestroy(plan->s_copy);
+            plan->s_copy = nullptr;
+            return cuda_status(e);
+        }
+    }
+    // Games per chunk: explicit, or chunks of at least 4 MiB and at most 16
+    // chunks.  The copy stream moves chunk k + 1 while `stream` computes
+    // chunk k, so only the last chunk's compute is added to the transfer.
+    int64_t chunk = plan->host_chunk;
+    if (chunk <= 0) {
+        const int64_t min_games = (int64_t)(((size_t)4 << 20) + vbytes - 1) / (int64_t)vbytes;
+        chunk = std::max(min_games, (B + 15) / 16);
+    }
+    chunk = std::min(std::max<int64_t>(chunk, 1), B);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemcpyAsync(plan->d_v_stage, v_host, vbytes * (size_t)B, cudaMemcpyHostToDevice, st);
+    // the staging buffer may still be read by earlier work on `stream`
+    cudaError_t e = cudaEventRecord(plan->ev_copy, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->s_copy, plan->ev_copy, 0);
     if (e != cudaSuccess) return cuda_status(e);
-    tt_fsi_status s = tt_fsi_apply(plan, plan->d_v_stage, B, plan->d_phi_stage, stream);
-    if (s != TT_FSI_OK) return s;
+    const char *src = static_cast<const char *>(v_host);
+    char *stage = static_cast<char *>(plan->d_v_stage);
+    char *phi_stage = static_cast<char *>(plan->d_phi_stage);
+    for (int64_t g0 = 0; g0 < B; g0 += chunk) {
+        const int64_t nb = std::min(chunk, B - g0);
+        e = cudaMemcpyAsync(stage + (size_t)g0 * vbytes, src + (size_t)g0 * vbytes, (size_t)nb * vbytes,
+                            cudaMemcpyHostToDevice, plan->s_copy);
+        // a wait takes the event's most recent record, so one event serves all chunks
+        if (e == cudaSuccess) e = cudaEventRecord(plan->ev_copy, plan->s_copy);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, plan->ev_copy, 0);
+        if (e != cudaSuccess) return cuda_status(e);
+        tt_fsi_status s = tt_fsi_apply(plan, stage + (size_t)g0 * vbytes, nb, phi_stage + (size_t)g0 * obytes, stream);
+        if (s != TT_FSI_OK) return s;
+    }
     e = cudaMemcpyAsync(phi_host, plan->d_phi_stage, obytes * (size_t)B, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return cuda_status(e);
+}
+
+tt_fsi_status tt_fsi_plan_set_host_chunk(tt_fsi_plan plan, int64_t games) {
+    if (!plan || games < 0) return TT_FSI_ERR_INVALID_ARG;
+    plan->host_chunk = games;
+    return TT_FSI_OK;
 }
 
 tt_fsi_status tt_fsi_plan_profile(tt_fsi_plan plan, int enable) {

@@ -136,6 +136,8 @@ def _declare(lib):
     lib.tt_fsi_status_string.argtypes = [i]
     lib.tt_fsi_apply_host.restype = i
     lib.tt_fsi_apply_host.argtypes = [vp, vp, i64, vp, vp]
+    lib.tt_fsi_plan_set_host_chunk.restype = i
+    lib.tt_fsi_plan_set_host_chunk.argtypes = [vp, i64]
     lib.tt_fsi_plan_profile.restype = i
     lib.tt_fsi_plan_profile.argtypes = [vp, i]
     lib.tt_fsi_plan_profile_read.restype = i

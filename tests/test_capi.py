@@ -56,3 +56,10 @@ def test_unknown_plan_flag_rejected_on_host():
     h = ctypes.c_void_p()
     assert lib.tt_fsi_plan_create_ex(10, 2, 0, 0, 1, 2, ctypes.byref(h)) == 1
     assert not h.value
+
+
+def test_host_chunk_setter_rejects_null_plan_on_host():
+    import ctypes
+    import paper_2601_01903_gb300 as fsi
+    lib = fsi.native.load()
+    assert lib.tt_fsi_plan_set_host_chunk(None, 1) == 1

@@ -252,3 +252,39 @@ def test_site_sweep_variant_matches_oracle(oracle_mod, arith, d, ell, B):
     got = plan.apply(_gpu(v)).cpu().numpy()
     plan.check()
     assert _rel_err(got, oracle_mod.fsi(v, d, ell), v) <= TOL
+
+
+@pytest.mark.parametrize("arith", ["exact", "f32"])
+@pytest.mark.parametrize("chunk", [0, 1, 3, 7])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_pipeline_matches_device_apply(oracle_mod, arith, chunk, pinned):
+    """tt_fsi_apply_host moves the input in chunks of whole games on its own
+    copy stream; every chunking gives the device path's scores bit for bit."""
+    d, ell, B = 15, 3, 7
+    v = _noise_games(d, B, seed=31)
+    dt = torch.float32 if arith == "f32" else torch.float64
+    plan = fsi.Plan(d, ell, arith, max_batch=B)
+    ref = plan.apply(_gpu(v, dt)).cpu()
+    plan.set_host_chunk(chunk)
+    vh = torch.as_tensor(v, dtype=dt)
+    if pinned:
+        vh = vh.pin_memory()
+    got = plan.apply_host(vh)
+    plan.check()
+    assert torch.equal(got, ref)
+    if arith == "exact":
+        assert _rel_err(got.numpy(), oracle_mod.fsi(v, d, ell), v) <= TOL
+    # a smaller batch through the same staging buffers
+    got2 = plan.apply_host(vh[2:5])
+    assert torch.equal(got2, ref[2:5])
+
+
+def test_host_pipeline_bad_arguments():
+    plan = fsi.Plan(10, 2, "exact", max_batch=2)
+    with pytest.raises(RuntimeError):
+        plan.set_host_chunk(-1)
+    with pytest.raises(ValueError):
+        plan.apply_host(torch.zeros((1, 1 << 10), dtype=torch.float64, device="cuda"))
+    with pytest.raises(RuntimeError):
+        plan.apply_host(torch.zeros((3, 1 << 10), dtype=torch.float64))
+    assert plan.apply_host(torch.zeros((0, 1 << 10), dtype=torch.float64)).shape == (0, plan.n_scores)
