@@ -92,5 +92,12 @@ TTFSI_HD constexpr int channel_base(int L, int SL) {
            rank4(c) * (13 - k8 - kC);
 }
 
+// Per-tile weight rows: one row of kWRow weights per (s, |S_L|, i) with
+// s <= L, |S_L| <= s, i <= s - |S_L| (s-major, then |S_L|, then i).
+constexpr int kWRow = 16;
+TTFSI_HD constexpr int wcombo_base(int s) { return s * (s + 1) * (s + 2) / 6; }
+TTFSI_HD constexpr int wcombo(int s, int sL, int i) { return wcombo_base(s) + sL * (s + 1) - sL * (sL - 1) / 2 + i; }
+TTFSI_HD constexpr int n_wcombo(int L) { return wcombo_base(L + 1); }
+
 }  // namespace fast
 }  // namespace ttfsi

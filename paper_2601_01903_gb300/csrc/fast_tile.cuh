@@ -61,6 +61,8 @@ struct FastArgs {
     int g_split31;        // exact weighting by 32 x 32-bit products (see the plan)
     int prefetch_ahead;   // tile launch: prefetch the tile this many CTAs ahead into L2 (0: off)
     long long game0;
+    const void *wstage;   // weight rows per u_H (see the plan); null when wstage_block == 0
+    int wstage_block;     // bytes per u_H, a multiple of 16
 };
 
 template <typename Acc>
@@ -315,6 +317,49 @@ __device__ __forceinline__ typename GTraits<Acc>::G fast_g_entry(const FastArgs 
     }
 }
 
+// Weight rows in shared memory per tile: int32 on the exact path (valid
+// when g_split31 holds: every weight plus the identity term fits), the
+// arithmetic's own type otherwise.  The plan holds the rows of every u_H;
+// a tile copies its u_H block with cp.async when it starts and waits for
+// the copy only before the ranked sums, so the copy costs no latency.
+template <typename Acc>
+struct WTraits {
+    using W = Acc;
+};
+template <>
+struct WTraits<long long> {
+    using W = int;
+};
+
+// One partial score from a staged row: sum over j < J = 13 - |S_L| of
+// w[j] Y(S_L, j).  Exact path: two 32 x 32-bit multiply-add chains on the
+// split channel y = yh 2^31 + yl.
+template <typename Acc, int J>
+__device__ __forceinline__ typename GTraits<Acc>::G fast_g_staged(const typename WTraits<Acc>::W *w, const Acc *y) {
+    using GT = typename GTraits<Acc>::G;
+    using WT = typename WTraits<Acc>::W;
+    Acc yv[J];
+    WT c[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) yv[j] = y[j];
+#pragma unroll
+    for (int j = 0; j < J; ++j) c[j] = w[j];
+    if constexpr (TileTraits<Acc>::exact) {
+        long long acc_h = 0, acc_l = 0;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            acc_h += (long long)c[j] * (int)(yv[j] >> 31);
+            acc_l += (long long)c[j] * (int)(yv[j] & 0x7fffffffll);
+        }
+        return (GT)(((unsigned __int128)(__int128)acc_h) << 31) + (GT)acc_l;
+    } else {
+        Acc acc = 0;
+#pragma unroll
+        for (int j = 0; j < J; ++j) acc += yv[j] * c[j];
+        return acc;
+    }
+}
+
 template <typename Acc, int L>
 __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long long game, const long long tile) {
     using In = typename TileTraits<Acc>::In;
@@ -323,10 +368,22 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
     Acc *regA = reinterpret_cast<Acc *>(smem_raw);  // tile, then one round's level-8 states
     Acc *regB = regA + fast::regA_elems(L);          // one round's level-4 states
     Acc *regY = regB + fast::regB_elems(L);          // channels
+    using WT = typename WTraits<Acc>::W;
+    WT *wst = reinterpret_cast<WT *>((reinterpret_cast<uintptr_t>(regY + fast::n_chan(L)) + 15) &
+                                     ~(uintptr_t)15);  // this tile's weight rows
     __shared__ int s_emax;
 
     const int tid = threadIdx.x;
     const In *src = reinterpret_cast<const In *>(a.v) + (game << a.d) + (tile << 12);
+    const int uH = __popcll((unsigned long long)tile);
+    const bool staged = a.wstage_block > 0;
+    if (staged) {
+        const char *wsrc = reinterpret_cast<const char *>(a.wstage) + (size_t)uH * a.wstage_block;
+        const unsigned wdst = (unsigned)__cvta_generic_to_shared(wst);
+        for (int o = tid * 16; o < a.wstage_block; o += kTileThreads * 16)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(wdst + o), "l"(wsrc + o) : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
 
     Acc x[16];
     int E = 0;
@@ -379,15 +436,33 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
     // ---- ranked sums: block 1 of round 0, then the rounds ----
     const int pos = t3 + 16 * t2;
     fast_block1<L, 0>(x, regB, pos);
+    // the weight rows are read only after this barrier
+    if (staged) asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     fast_round<L, 0>(x, regA, regB, regY, tid, pos);
     // ---- partial scores G(S_L, s, i) of this tile ----
-    const int uH = __popcll((unsigned long long)tile);
     const int P1 = a.h + 1, Q1 = 13;
     // partial scores of a game are stored entry-major, [n_g][2^h tiles], so
     // that the combine's lanes (consecutive tiles) read consecutive addresses
     const long long ntile = 1ll << a.h;
     GT *gdst = reinterpret_cast<GT *>(a.G) + (game << a.h) * (long long)a.n_g + tile;
+    if (staged) {
+        for (int g = tid; g < a.n_g; g += kTileThreads) {
+            const int cb = __ldg(a.gtab + 2 * g), code = __ldg(a.gtab + 2 * g + 1);
+            const int sL = code & 0xff, s = (code >> 8) & 0xff, i = code >> 16;
+            const WT *w = wst + fast::wcombo(s, sL, i) * fast::kWRow;
+            GT acc;
+            // entries are sorted by |S_L|, so a warp almost always takes one case
+            switch (sL) {
+                case 0: acc = fast_g_staged<Acc, 13>(w, regY + cb); break;
+                case 1: acc = fast_g_staged<Acc, 12>(w, regY + cb); break;
+                case 2: acc = fast_g_staged<Acc, 11>(w, regY + cb); break;
+                case 3: acc = fast_g_staged<Acc, 10>(w, regY + cb); break;
+                default: acc = fast_g_staged<Acc, 9>(w, regY + cb); break;
+            }
+            gdst[g * ntile] = acc;
+        }
+    } else
     for (int g = tid; g < a.n_g; g += kTileThreads) {
         const int cb = __ldg(a.gtab + 2 * g), code = __ldg(a.gtab + 2 * g + 1);
         const int sL = code & 0xff, s = (code >> 8) & 0xff, i = code >> 16;

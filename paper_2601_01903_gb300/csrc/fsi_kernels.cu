@@ -516,7 +516,7 @@ struct TableRef {
     size_t bytes;
 };
 
-constexpr int kPlanTables = 7;
+constexpr int kPlanTables = 8;
 
 std::array<TableRef, kPlanTables> plan_tables(Plan &p) {
     return {{
@@ -527,6 +527,7 @@ std::array<TableRef, kPlanTables> plan_tables(Plan &p) {
         {(void **)&p.d_wf64, p.wf64.data(), p.wf64.size() * sizeof(double)},
         {(void **)&p.d_wf32, p.wf32.data(), p.wf32.size() * sizeof(float)},
         {(void **)&p.d_gtab, p.gtab.data(), p.gtab.size() * sizeof(int32_t)},
+        {(void **)&p.d_wstage, p.wstage.data(), p.wstage.size()},
     }};
 }
 
@@ -553,6 +554,7 @@ void free_plan_device(Plan *p) {
     cudaFree(p->d_exp);
     cudaFree(p->d_err);
     cudaFree(p->d_gtab);
+    cudaFree(p->d_wstage);
     cudaFree(p->d_counters);
 }
 
@@ -571,6 +573,8 @@ FastArgs fast_args(const Plan &p) {
     fa.prec_bits = p.prec_bits;
     fa.load_mask = (1 << p.load_bits) - 1;
     fa.g_split31 = p.g_split31 ? 1 : 0;
+    fa.wstage = p.d_wstage;
+    fa.wstage_block = p.wstage_block;
     return fa;
 }
 
@@ -625,7 +629,7 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
                            cudaEvent_t ev2 = nullptr) {
     // every table a kernel of this plan will read must be in place
     const bool exact = TileTraits<Acc>::exact;
-    if (!p.d_tasks || !p.d_Y || !p.d_err || (p.fast12 && !p.d_gtab) ||
+    if (!p.d_tasks || !p.d_Y || !p.d_err || (p.fast12 && !p.d_gtab) || (p.wstage_block > 0 && !p.d_wstage) ||
         (!p.mob_only && !p.fast12 && !p.d_trans) ||
         (exact && (!p.d_wnum || !p.d_wden || !p.d_exp)) ||
         (!exact && sizeof(Acc) == 8 && !p.d_wf64) || (!exact && sizeof(Acc) == 4 && !p.d_wf32))

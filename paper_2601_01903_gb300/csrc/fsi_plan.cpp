@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <tuple>
 
@@ -254,7 +255,11 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
         if (fast::n_chan(p.ell_eff) != p.n_ch) return TT_FSI_ERR_UNSUPPORTED;  // layouts disagree
         p.fast_regA = fast::regA_elems(p.ell_eff);
         p.fast_regB = fast::regB_elems(p.ell_eff);
-        p.smem_fast = (size_t)(p.fast_regA + p.fast_regB + p.n_ch) * elem;
+        // tile states and channels, then the tile's weight rows (int32 on the
+        // exact path, the arithmetic's own type otherwise)
+        const size_t wbytes = (arith == TT_FSI_ARITH_F64) ? 8 : 4;
+        p.smem_fast = (size_t)(p.fast_regA + p.fast_regB + p.n_ch) * elem + 16 +
+                      (size_t)fast::n_wcombo(p.ell_eff) * fast::kWRow * wbytes;
         p.fast12 = p.smem_fast <= smem_budget;
     }
 
@@ -393,6 +398,47 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
         const __int128 yh_max = (ymax >> 31) + 1, lim = (__int128)1 << 63;
         p.g_split31 = cmax < (1ll << 31) && yh_max < ((__int128)1 << 31) &&
                       (__int128)13 * cmax * ((__int128)1 << 31) < lim && (__int128)13 * cmax * yh_max < lim;
+    }
+
+    // Weight rows of the fast path per u_H: row (s, |S_L|, i) holds, for
+    // j <= 12 - |S_L|, (-1)^(r - i) [omega_s(u_H + r - i, |S_L| + j) + [i = u_H][j = 0]]
+    // (r = s - |S_L|; the identity term is D_s on the exact path), and zeros
+    // where no score of such a tile uses the row (i > u_H or r - i > h - u_H).
+    p.wstage.clear();
+    p.wstage_block = 0;
+    if (p.fast12 && (arith != TT_FSI_ARITH_EXACT || p.g_split31)) {
+        const int L = p.ell_eff;
+        const size_t wb = (arith == TT_FSI_ARITH_F64) ? 8 : 4;
+        p.wstage_block = (int)((size_t)fast::n_wcombo(L) * fast::kWRow * wb);
+        p.wstage.assign((size_t)(p.h + 1) * p.wstage_block, 0);
+        for (int uH = 0; uH <= p.h; ++uH)
+            for (int s = 0; s <= L; ++s)
+                for (int sL = 0; sL <= s; ++sL)
+                    for (int i = 0; i <= s - sL; ++i) {
+                        const int r = s - sL;
+                        if (i > uH || r - i > p.h - uH) continue;
+                        const size_t wo = ((size_t)s * P1 + (uH + r - i)) * Q1 + sL;
+                        const bool neg = (r - i) & 1, ident = (i == uH);
+                        uint8_t *row = p.wstage.data() + (size_t)uH * p.wstage_block +
+                                       (size_t)fast::wcombo(s, sL, i) * fast::kWRow * wb;
+                        for (int j = 0; j <= b - sL; ++j) {
+                            if (arith == TT_FSI_ARITH_EXACT) {
+                                long long w = p.wnum[wo + j] + ((j == 0 && ident) ? p.wden[s] : 0);
+                                const int32_t c = (int32_t)(neg ? -w : w);
+                                std::memcpy(row + j * wb, &c, wb);
+                            } else if (arith == TT_FSI_ARITH_F32) {
+                                float w = p.wf32[wo + j];
+                                if (j == 0 && ident) w += 1.0f;
+                                const float c = neg ? -w : w;
+                                std::memcpy(row + j * wb, &c, wb);
+                            } else {
+                                double w = p.wf64[wo + j];
+                                if (j == 0 && ident) w += 1.0;
+                                const double c = neg ? -w : w;
+                                std::memcpy(row + j * wb, &c, wb);
+                            }
+                        }
+                    }
     }
     return TT_FSI_OK;
 }

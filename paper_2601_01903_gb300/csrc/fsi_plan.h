@@ -94,6 +94,12 @@ struct Plan {
     int32_t *d_trans = nullptr;
     int32_t *d_tasks = nullptr;
     long long *d_wnum = nullptr;
+    // fast path: weight rows per u_H = |U_H| ([h + 1][n_wcombo][kWRow], int32
+    // on the exact split path, float / double otherwise), copied into shared
+    // memory by each tile; empty when the exact path needs 64-bit weights
+    std::vector<uint8_t> wstage;
+    int wstage_block = 0;  // bytes per u_H
+    void *d_wstage = nullptr;
     long long *d_wden = nullptr;
     double *d_wf64 = nullptr;
     float *d_wf32 = nullptr;
