@@ -405,8 +405,17 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
         const bool bad = (E == 0x7ff);
         if (bad && tid == 0) atomicOr(a.err, kErrNonFinite);
         if (E == 0) E = 1;
+        if (bad) {
 #pragma unroll
-        for (int r = 0; r < 16; ++r) x[r] = bad ? 0ll : to_fixed(raw[r], E, a.prec_bits);
+            for (int r = 0; r < 16; ++r) x[r] = 0;
+        } else if (E >= a.prec_bits + 1) {  // every tile but one of tiny values
+            const int C = 53 - a.prec_bits + E;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) x[r] = to_fixed_big_tile(raw[r], C);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) x[r] = to_fixed(raw[r], E, a.prec_bits);
+        }
     } else {
 #pragma unroll
         for (int r = 0; r < 16; ++r) x[r] = (Acc)__ldg(src + ((tid + 256 * r) & a.load_mask));

@@ -374,6 +374,8 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
     p.prec_bits = 62 - (int)std::ceil(b * std::log2(3.0));
     if (p.mob_only) p.prec_bits = 62 - b;
     p.prec_bits = std::min(p.prec_bits, 53);  // never finer than the float64 mantissa
+    // the fast tile kernel's branch-free conversion needs P <= 52 (P = 42 at b = 12)
+    if (p.fast12 && p.prec_bits > 52) return TT_FSI_ERR_UNSUPPORTED;
     // Cross-tile alignment: a score is at most 2^l max|v| in magnitude (the
     // operator's row L1 norm), so after scaling by 2^shift and the weight
     // denominator it must stay below 2^126.

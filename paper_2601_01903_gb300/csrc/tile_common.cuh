@@ -35,6 +35,23 @@ __device__ __forceinline__ long long to_fixed(unsigned long long bits, int E, in
     return (bits >> 63) ? -x : x;
 }
 
+// to_fixed for a tile whose largest biased exponent E satisfies E >= P + 1
+// (and P <= 52), with C = 53 - P + E: the shift C - e is then at least 1,
+// and a zero or subnormal input (e = 0) has C >= 54, so it rounds to 0
+// whether or not the implicit bit is set.  Same results as to_fixed, with no
+// branches: the implicit bit is always set, the shift is capped at 54 (any
+// shift of at least 54 already gives 0) and the sign is applied as
+// (r ^ s) - s.
+__device__ __forceinline__ long long to_fixed_big_tile(unsigned long long bits, int C) {
+    const unsigned hi = (unsigned)(bits >> 32);
+    const int e = (int)((hi >> 20) & 0x7ff);
+    const unsigned long long mant = (bits & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = min(C - e, 54);
+    const long long r = (long long)(((mant >> (sh - 1)) + 1) >> 1);
+    const long long sg = (long long)((int)hi >> 31);
+    return (r ^ sg) - sg;
+}
+
 template <typename Acc>
 struct TileTraits;
 template <>

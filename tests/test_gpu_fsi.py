@@ -148,6 +148,34 @@ def test_scale_invariance_of_exact_path(oracle_mod):
     assert _rel_err(got, oracle_mod.fsi(v, d, 2), v) <= TOL
 
 
+@pytest.mark.parametrize("d,ell", [(16, 2), (14, 3)])
+def test_tiny_tiles_and_subnormals(oracle_mod, d, ell):
+    """A tile whose largest value is below 2^-980 (the exact path's general
+    conversion) and a tile mixing normal values with zeros and subnormals
+    (the branch-free conversion) against the oracle."""
+    v = _noise_games(d, 1, seed=11, v0=False)
+    v[0, 2 << 12: 3 << 12] *= 2.0 ** -1000
+    v[0, 3 << 12: (3 << 12) + 64] = 5e-324
+    v[0, (3 << 12) + 64: (3 << 12) + 96] = 0.0
+    got, _ = _run(v, d, ell, "exact")
+    assert _rel_err(got, oracle_mod.fsi(v, d, ell), v) <= TOL
+
+
+@pytest.mark.parametrize("k", [-990, -600, 600])
+def test_power_of_two_scaling_is_exact(k):
+    """Scaling a game by 2^k moves every tile across the conversion's two
+    branches (k = -990 leaves only tiny tiles) without changing the integer
+    arithmetic: the scores scale by 2^k bit for bit."""
+    d, ell = 15, 3
+    v = _noise_games(d, 2, seed=12, v0=False)
+    got, _ = _run(v, d, ell, "exact")
+    got_s, _ = _run(v * 2.0 ** k, d, ell, "exact")
+    ref = got * 2.0 ** k
+    normal = np.abs(ref) >= 2.0 ** -1022   # a subnormal output loses bits when written
+    assert normal.mean() > 0.99
+    assert np.array_equal(got_s[normal], ref[normal])
+
+
 def test_nonfinite_input_is_reported():
     v = _noise_games(10, 1, seed=1)
     v[0, 77] = np.inf
