@@ -153,37 +153,64 @@ __device__ __forceinline__ void fast_block1(const Acc (&x)[16], Acc *regB, int p
     }
 }
 
-// Block 2 of round RD: items (rank sigma_A, u), u in [RD, 8], 16 lanes over
-// tau_C.  Level-8 states go to regA[tau_C * NST + state].
-template <int L, int RD, typename Acc>
-__device__ __forceinline__ void fast_block2(const Acc *regB, Acc *regA, int tid) {
+// Block 2 item (rank sigma_A = rA, u = RD + uu) of round RD on lane tau_C:
+// gathers the 16 level-4 states Z_A(sigma_A, u - |tau_B|; tau_B), zero where
+// that rank is outside [RD, 4], and writes the level-8 states (sigma_A u
+// sigma_B, u) to regA[tau_C * NST + state].  UU >= 0 fixes uu at compile
+// time, so the zero inputs and the states that cannot exist fold away;
+// UU = -1 takes uu at run time.
+template <int L, int RD, int UU, typename Acc>
+__device__ __forceinline__ void fast_block2_item(const Acc *regB, Acc *regA, int rA, int uu_rt, int t3) {
     constexpr int O = L - RD;
-    constexpr int NU = 9 - RD;
-    constexpr int NIT = fast::c4(RD) * NU;
     constexpr int S8 = fast::s8(L, RD);
     constexpr int NST = fast::nst(L);
+    const int uu = UU >= 0 ? UU : uu_rt;
+    // input tau_B: level-4 state (sigma_A, t = u - |tau_B|), t in [RD, 4]
+    const Acc *src = regB + (rA * (5 - RD) + uu) * 256 + t3;
+    Acc x[16];
+#pragma unroll
+    for (int tau = 0; tau < 16; ++tau) {
+        const int pc = fast::pc4(tau);
+        Acc val = 0;
+        if (uu >= pc && uu - pc <= 4 - RD) val = src[16 * tau - 256 * pc];
+        x[tau] = val;
+    }
+    zeta16<O>(x);
+    Acc *dst = regA + t3 * NST + rA * S8 + uu;
+#pragma unroll
+    for (int sb = 0; sb < 16; ++sb) {
+        const int kB = fast::pc4(sb);
+        if (kB > O) continue;
+        // state (sigma_A u sigma_B, u): off8 + rank * (9 - RD - kB) + (u - RD - kB)
+        if (uu >= kB) dst[fast::off8(RD, kB) + fast::rank4(sb) * (9 - RD - kB) - kB] = x[sb];
+    }
+}
+
+// Block 2 of round RD: items (rank sigma_A, u), u in [RD, 8], 16 lanes over
+// tau_C.  Items run in the order (k, rank sigma_A) with uu = k / 2 for even
+// k and 8 - RD - k / 2 for odd k: the items with uu in {0, 1, 7 - RD, 8 - RD}
+// (at most 5 of their 16 inputs nonzero) come first and run bodies compiled
+// for their uu, and the two half-warps of a warp take the same uu whenever
+// the number of sigma_A is even (for one sigma_A they pair uu with 8 - RD - uu).
+template <int L, int RD, typename Acc>
+__device__ __forceinline__ void fast_block2(const Acc *regB, Acc *regA, int tid) {
+    constexpr int NU = 9 - RD;
+    constexpr int NA = fast::c4(RD);
+    constexpr int NIT = NA * NU;
     const int t3 = tid & 15;
     for (int it = tid >> 4; it < NIT; it += kTileThreads / 16) {
-        const int rA = it / NU, uu = it - rA * NU;  // u = RD + uu
-        // input tau_B: level-4 state (sigma_A, t = u - |tau_B|), t in [RD, 4]
-        const Acc *src = regB + (rA * (5 - RD) + uu) * 256 + t3;
-        Acc x[16];
-#pragma unroll
-        for (int tau = 0; tau < 16; ++tau) {
-            const int pc = fast::pc4(tau);
-            Acc val = 0;
-            if (uu >= pc && uu - pc <= 4 - RD) val = src[16 * tau - 256 * pc];
-            x[tau] = val;
-        }
-        zeta16<O>(x);
-        Acc *dst = regA + t3 * NST + rA * S8 + uu;
-#pragma unroll
-        for (int sb = 0; sb < 16; ++sb) {
-            const int kB = fast::pc4(sb);
-            if (kB > O) continue;
-            // state (sigma_A u sigma_B, u): off8 + rank * (9 - RD - kB) + (u - RD - kB)
-            if (uu >= kB) dst[fast::off8(RD, kB) + fast::rank4(sb) * (9 - RD - kB) - kB] = x[sb];
-        }
+        const int k = it / NA, rA = it - k * NA;
+        const int uu = (k & 1) ? NU - 1 - (k >> 1) : (k >> 1);
+        if (uu == 0)
+            fast_block2_item<L, RD, 0>(regB, regA, rA, uu, t3);
+        else if (uu == 1)
+            fast_block2_item<L, RD, 1>(regB, regA, rA, uu, t3);
+        else if (uu == NU - 2)
+            fast_block2_item<L, RD, NU - 2>(regB, regA, rA, uu, t3);
+        else if (uu == NU - 1)
+            fast_block2_item<L, RD, NU - 1>(regB, regA, rA, uu, t3);
+        else
+            fast_block2_item<L, RD, -1>(regB, regA, rA, uu, t3);
     }
 }
 
@@ -461,13 +488,22 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
             const int sL = code & 0xff, s = (code >> 8) & 0xff, i = code >> 16;
             const WT *w = wst + fast::wcombo(s, sL, i) * fast::kWRow;
             GT acc;
-            // entries are sorted by |S_L|, so a warp almost always takes one case
-            switch (sL) {
-                case 0: acc = fast_g_staged<Acc, 13>(w, regY + cb); break;
-                case 1: acc = fast_g_staged<Acc, 12>(w, regY + cb); break;
-                case 2: acc = fast_g_staged<Acc, 11>(w, regY + cb); break;
-                case 3: acc = fast_g_staged<Acc, 10>(w, regY + cb); break;
-                default: acc = fast_g_staged<Acc, 9>(w, regY + cb); break;
+            if constexpr (TileTraits<Acc>::exact) {
+                // 13 products for every entry: the row's weights past
+                // 12 - |S_L| are zero, and the channels read there (the next
+                // channel's, or past the last channel the alignment gap and
+                // the weight rows, all inside the allocation) are integers,
+                // so every entry runs the same code
+                acc = fast_g_staged<Acc, 13>(w, regY + cb);
+            } else {
+                // entries are sorted by |S_L|, so a warp almost always takes one case
+                switch (sL) {
+                    case 0: acc = fast_g_staged<Acc, 13>(w, regY + cb); break;
+                    case 1: acc = fast_g_staged<Acc, 12>(w, regY + cb); break;
+                    case 2: acc = fast_g_staged<Acc, 11>(w, regY + cb); break;
+                    case 3: acc = fast_g_staged<Acc, 10>(w, regY + cb); break;
+                    default: acc = fast_g_staged<Acc, 9>(w, regY + cb); break;
+                }
             }
             gdst[g * ntile] = acc;
         }
