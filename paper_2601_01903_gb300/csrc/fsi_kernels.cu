@@ -161,6 +161,7 @@ struct CombineFastArgs {
     const int *tile_exp;
     const int32_t *tasks;
     const long long *wden;
+    const double *winv;  // 1 / wden[s]
     void *phi;
     int h, n_g, shift_cap;
     long long n_out;
@@ -172,6 +173,44 @@ __device__ __forceinline__ __int128 shfl_down_i128(__int128 v, int o) {
     lo = __shfl_down_sync(0xffffffffu, lo, o);
     hi = __shfl_down_sync(0xffffffffu, hi, o);
     return (__int128)(((unsigned __int128)hi << 64) | lo);
+}
+
+// x 2^-F rounded to the nearest double (ties to even) with integer
+// instructions only (float64 is slow on this part): the leading one of |x|
+// gives the exponent, the next 52 bits the mantissa, the rest the rounding.
+// Returns false when the result is not a normal double (the caller then
+// takes the float64 route); |x| < 2^127.
+__device__ __forceinline__ bool i128_scaled_to_double(__int128 x, int F, double &out) {
+    if (x == 0) {
+        out = 0.0;
+        return true;
+    }
+    const unsigned long long sign = x < 0 ? (1ull << 63) : 0ull;
+    const unsigned __int128 u = x < 0 ? (unsigned __int128)(-x) : (unsigned __int128)x;
+    const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+    const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);  // 0 .. 127
+    unsigned long long top, rest;  // |x| << lz: bits 127..64 and 63..0
+    if (lz >= 64) {
+        top = lo << (lz - 64);
+        rest = 0;
+    } else if (lz == 0) {
+        top = hi;
+        rest = lo;
+    } else {
+        top = (hi << lz) | (lo >> (64 - lz));
+        rest = lo << lz;
+    }
+    unsigned long long mant = top >> 11;  // 53 bits, leading one at bit 52
+    const unsigned long long low11 = top & 0x7ff;
+    mant += (low11 > 0x400 || (low11 == 0x400 && (rest != 0 || (mant & 1)))) ? 1 : 0;
+    int e = 127 - lz - F;
+    if (mant >> 53) {
+        mant >>= 1;
+        ++e;
+    }
+    if (e < -1022 || e > 1023) return false;
+    out = __longlong_as_double((long long)(sign | ((unsigned long long)(e + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+    return true;
 }
 
 // Scores [task_begin, task_end) of one game; warp w takes task_begin + w,
@@ -202,6 +241,10 @@ __device__ __forceinline__ void combine_fast_body(const CombineFastArgs &a, cons
         atomicMax(&s_fmax, fmax);
         __syncthreads();
         const int Fc = min(s_fmax, s_fmin + a.shift_cap);
+        // When the game's tile exponents span at most shift_cap (all but games
+        // of extreme dynamic range), Fc = fmax and every alignment is a left
+        // shift by 0 .. shift_cap < 64: two 64-bit shifts, no rounding.
+        const bool left_only = s_fmax - s_fmin <= a.shift_cap;
         constexpr int U = 8;  // independent loads in flight per lane
         for (long long task = task_begin + warp; task < task_end; task += kCombineFastWarps) {
             const unsigned SH = (unsigned)a.tasks[task * 4 + 1];
@@ -223,22 +266,42 @@ __device__ __forceinline__ void combine_fast_body(const CombineFastArgs &a, cons
                         f[k] = Fc;
                     }
                 }
+                if (left_only) {
 #pragma unroll
-                for (int k = 0; k < U; ++k) {
-                    __int128 g = (__int128)(((unsigned __int128)(unsigned long long)raw[k].y << 64) |
-                                            (unsigned long long)raw[k].x);
-                    const int delta = Fc - f[k];
-                    if (delta >= 0)
-                        g = (__int128)((unsigned __int128)g << delta);
-                    else
-                        g = (-delta >= 127) ? (__int128)0 : ((g + ((__int128)1 << (-delta - 1))) >> (-delta));
-                    acc += g;
+                    for (int k = 0; k < U; ++k) {
+                        const int delta = Fc - f[k];  // 0 .. shift_cap (0 for the padding slots)
+                        const unsigned long long lo = (unsigned long long)raw[k].x;
+                        const unsigned long long hi =
+                            ((unsigned long long)raw[k].y << delta) | ((lo >> 1) >> (63 - delta));
+                        acc += (__int128)(((unsigned __int128)hi << 64) | (lo << delta));
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < U; ++k) {
+                        __int128 g = (__int128)(((unsigned __int128)(unsigned long long)raw[k].y << 64) |
+                                                (unsigned long long)raw[k].x);
+                        const int delta = Fc - f[k];
+                        if (delta >= 0)
+                            g = (__int128)((unsigned __int128)g << delta);
+                        else
+                            g = (-delta >= 127) ? (__int128)0 : ((g + ((__int128)1 << (-delta - 1))) >> (-delta));
+                        acc += g;
+                    }
                 }
             }
             for (int o = 16; o > 0; o >>= 1) acc += shfl_down_i128(acc, o);
             if (lane == 0) {
-                const double r = i128_to_double(acc) / (double)a.wden[s];
-                reinterpret_cast<double *>(a.phi)[game * a.n_out + task] = ldexp(r, -Fc);
+                // phi = acc 2^-Fc / D_s.  Float64 is slow on this part: acc 2^-Fc
+                // is rounded to a double with integer instructions and the
+                // quotient is a product with 1 / D_s (rounded once on the host),
+                // one float64 instruction per score; ldexp where acc 2^-Fc is
+                // not a normal double.
+                double x, out;
+                if (i128_scaled_to_double(acc, Fc, x))
+                    out = x * __ldg(a.winv + s);
+                else
+                    out = ldexp(i128_to_double(acc) * __ldg(a.winv + s), -Fc);
+                reinterpret_cast<double *>(a.phi)[game * a.n_out + task] = out;
             }
         }
     } else {
@@ -516,7 +579,7 @@ struct TableRef {
     size_t bytes;
 };
 
-constexpr int kPlanTables = 8;
+constexpr int kPlanTables = 9;
 
 std::array<TableRef, kPlanTables> plan_tables(Plan &p) {
     return {{
@@ -528,6 +591,7 @@ std::array<TableRef, kPlanTables> plan_tables(Plan &p) {
         {(void **)&p.d_wf32, p.wf32.data(), p.wf32.size() * sizeof(float)},
         {(void **)&p.d_gtab, p.gtab.data(), p.gtab.size() * sizeof(int32_t)},
         {(void **)&p.d_wstage, p.wstage.data(), p.wstage.size()},
+        {(void **)&p.d_winv, p.winv.data(), p.winv.size() * sizeof(double)},
     }};
 }
 
@@ -555,6 +619,7 @@ void free_plan_device(Plan *p) {
     cudaFree(p->d_err);
     cudaFree(p->d_gtab);
     cudaFree(p->d_wstage);
+    cudaFree(p->d_winv);
     cudaFree(p->d_counters);
 }
 
@@ -585,6 +650,7 @@ CombineFastArgs combine_fast_args(const Plan &p) {
     cf.tile_exp = p.d_exp;
     cf.tasks = p.d_tasks;
     cf.wden = p.d_wden;
+    cf.winv = p.d_winv;
     cf.h = p.h;
     cf.n_g = p.n_g;
     cf.shift_cap = p.shift_cap;
@@ -631,7 +697,7 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
     const bool exact = TileTraits<Acc>::exact;
     if (!p.d_tasks || !p.d_Y || !p.d_err || (p.fast12 && !p.d_gtab) || (p.wstage_block > 0 && !p.d_wstage) ||
         (!p.mob_only && !p.fast12 && !p.d_trans) ||
-        (exact && (!p.d_wnum || !p.d_wden || !p.d_exp)) ||
+        (exact && (!p.d_wnum || !p.d_wden || !p.d_winv || !p.d_exp)) ||
         (!exact && sizeof(Acc) == 8 && !p.d_wf64) || (!exact && sizeof(Acc) == 4 && !p.d_wf32))
         return TT_FSI_ERR_INVALID_ARG;
     TileArgs ta{};
@@ -735,6 +801,7 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
             cf.tile_exp = p.d_exp;
             cf.tasks = p.d_tasks;
             cf.wden = p.d_wden;
+            cf.winv = p.d_winv;
             cf.phi = phi;
             cf.h = p.h;
             cf.n_g = p.n_g;
@@ -1471,6 +1538,7 @@ tt_fsi_status tt_fsi_batch_create_index(const tt_fsi_game *games_host, int64_t n
         ca = CombineFastArgs{};
         ca.tasks = p.d_tasks;
         ca.wden = p.d_wden;
+        ca.winv = p.d_winv;
         ca.h = p.h;
         ca.n_g = p.n_g;
         ca.shift_cap = p.shift_cap;

@@ -368,6 +368,9 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
             }
     }
 
+    p.winv.resize(S1);
+    for (int s = 0; s < S1; ++s) p.winv[s] = 1.0 / (double)p.wden[s];
+
     // Fixed-point headroom: a tile's ranked sums are bounded by 3^b max|V|
     // (row L1 norm 2^|S_L| C(b-|S_L|, j) 2^j <= 3^b), so |V| < 2^P with
     // P = 62 - ceil(b log2 3) keeps every tile result inside int64.

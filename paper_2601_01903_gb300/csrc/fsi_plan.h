@@ -94,6 +94,8 @@ struct Plan {
     int32_t *d_trans = nullptr;
     int32_t *d_tasks = nullptr;
     long long *d_wnum = nullptr;
+    std::vector<double> winv;  // exact path: 1 / den[s], rounded once (the combine's scale)
+    double *d_winv = nullptr;
     // fast path: weight rows per u_H = |U_H| ([h + 1][n_wcombo][kWRow], int32
     // on the exact split path, float / double otherwise), copied into shared
     // memory by each tile; empty when the exact path needs 64-bit weights
