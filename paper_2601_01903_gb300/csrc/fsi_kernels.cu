@@ -51,6 +51,7 @@ struct CombineArgs {
     const int32_t *tasks;
     const long long *wnum;
     const long long *wden;
+    const double *winv;  // 1 / wden[s]
     const double *wf64;
     const float *wf32;
     void *phi;
@@ -514,8 +515,14 @@ __global__ void __launch_bounds__(kCombineThreads) fsi_combine_kernel(CombineArg
             __syncthreads();
         }
         if (tid == 0) {
-            double r = i128_to_double(red[0]) / (double)den;
-            reinterpret_cast<double *>(a.phi)[game * a.n_out + task] = ldexp(r, -Fc);
+            // as in the fast combine: acc 2^-Fc rounded with integer
+            // instructions, then one product with 1 / D_s
+            double x, out;
+            if (i128_scaled_to_double(red[0], Fc, x))
+                out = x * a.winv[s];
+            else
+                out = ldexp(i128_to_double(red[0]) * a.winv[s], -Fc);
+            reinterpret_cast<double *>(a.phi)[game * a.n_out + task] = out;
         }
     } else {
         __shared__ Acc red[kCombineThreads];
@@ -723,6 +730,7 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
     ca.tasks = p.d_tasks;
     ca.wnum = p.d_wnum;
     ca.wden = p.d_wden;
+    ca.winv = p.d_winv;
     ca.wf64 = p.d_wf64;
     ca.wf32 = p.d_wf32;
     ca.phi = phi;
