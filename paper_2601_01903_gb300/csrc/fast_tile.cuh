@@ -387,6 +387,21 @@ __device__ __forceinline__ typename GTraits<Acc>::G fast_g_staged(const typename
     }
 }
 
+// Exact path with 64-bit weight rows (numerators beyond the split): full
+// 64 x 64 -> 128-bit products.
+template <int J>
+__device__ __forceinline__ __int128 fast_g_staged64(const long long *w, const long long *y) {
+    long long yv[J], c[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) yv[j] = y[j];
+#pragma unroll
+    for (int j = 0; j < J; ++j) c[j] = w[j];
+    __int128 acc = 0;
+#pragma unroll
+    for (int j = 0; j < J; ++j) acc += mul_wide(yv[j], c[j]);
+    return acc;
+}
+
 template <typename Acc, int L>
 __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long long game, const long long tile) {
     using In = typename TileTraits<Acc>::In;
@@ -494,7 +509,12 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
                 // channel's, or past the last channel the alignment gap and
                 // the weight rows, all inside the allocation) are integers,
                 // so every entry runs the same code
-                acc = fast_g_staged<Acc, 13>(w, regY + cb);
+                if (a.g_split31)
+                    acc = fast_g_staged<Acc, 13>(w, regY + cb);
+                else
+                    acc = fast_g_staged64<13>(reinterpret_cast<const long long *>(wst) +
+                                                  fast::wcombo(s, sL, i) * fast::kWRow,
+                                              reinterpret_cast<const long long *>(regY) + cb);
             } else {
                 // entries are sorted by |S_L|, so a warp almost always takes one case
                 switch (sL) {

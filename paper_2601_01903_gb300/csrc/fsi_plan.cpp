@@ -255,9 +255,9 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
         if (fast::n_chan(p.ell_eff) != p.n_ch) return TT_FSI_ERR_UNSUPPORTED;  // layouts disagree
         p.fast_regA = fast::regA_elems(p.ell_eff);
         p.fast_regB = fast::regB_elems(p.ell_eff);
-        // tile states and channels, then the tile's weight rows (int32 on the
-        // exact path, the arithmetic's own type otherwise)
-        const size_t wbytes = (arith == TT_FSI_ARITH_F64) ? 8 : 4;
+        // tile states and channels, then the tile's weight rows (int32 or
+        // int64 on the exact path, the arithmetic's own type otherwise)
+        const size_t wbytes = (arith == TT_FSI_ARITH_F32) ? 4 : 8;
         p.smem_fast = (size_t)(p.fast_regA + p.fast_regB + p.n_ch) * elem + 16 +
                       (size_t)fast::n_wcombo(p.ell_eff) * fast::kWRow * wbytes;
         p.fast12 = p.smem_fast <= smem_budget;
@@ -411,9 +411,11 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
     // where no score of such a tile uses the row (i > u_H or r - i > h - u_H).
     p.wstage.clear();
     p.wstage_block = 0;
-    if (p.fast12 && (arith != TT_FSI_ARITH_EXACT || p.g_split31)) {
+    if (p.fast12) {
         const int L = p.ell_eff;
-        const size_t wb = (arith == TT_FSI_ARITH_F64) ? 8 : 4;
+        // exact: int32 when the split weighting applies, else int64
+        // (|numerator| < 2^62 and D_s < 2^60, so the sum fits)
+        const size_t wb = (arith == TT_FSI_ARITH_F32 || (arith == TT_FSI_ARITH_EXACT && p.g_split31)) ? 4 : 8;
         p.wstage_block = (int)((size_t)fast::n_wcombo(L) * fast::kWRow * wb);
         p.wstage.assign((size_t)(p.h + 1) * p.wstage_block, 0);
         for (int uH = 0; uH <= p.h; ++uH)
@@ -429,8 +431,13 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
                         for (int j = 0; j <= b - sL; ++j) {
                             if (arith == TT_FSI_ARITH_EXACT) {
                                 long long w = p.wnum[wo + j] + ((j == 0 && ident) ? p.wden[s] : 0);
-                                const int32_t c = (int32_t)(neg ? -w : w);
-                                std::memcpy(row + j * wb, &c, wb);
+                                w = neg ? -w : w;
+                                if (wb == 4) {
+                                    const int32_t c = (int32_t)w;
+                                    std::memcpy(row + j * wb, &c, wb);
+                                } else {
+                                    std::memcpy(row + j * wb, &w, wb);
+                                }
                             } else if (arith == TT_FSI_ARITH_F32) {
                                 float w = p.wf32[wo + j];
                                 if (j == 0 && ident) w += 1.0f;
