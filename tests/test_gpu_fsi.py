@@ -205,7 +205,7 @@ def test_repeated_calls_are_bitwise_identical():
 
 
 @pytest.mark.parametrize("arith", ["exact", "f64", "f32"])
-@pytest.mark.parametrize("d,ell,B", [(14, 3, 5), (20, 2, 2), (9, 3, 7), (16, 1, 3), (13, 3, 1)])
+@pytest.mark.parametrize("d,ell,B", [(14, 3, 5), (20, 2, 2), (9, 3, 7), (16, 1, 3), (13, 3, 1), (17, 4, 2)])
 def test_fused_schedule_matches_two_launches(arith, d, ell, B):
     """The fused persistent launch and the tile-then-combine launches run the
     same per-tile and per-score code: results are bitwise identical."""
