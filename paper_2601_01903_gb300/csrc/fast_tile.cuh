@@ -61,7 +61,7 @@ struct FastArgs {
     int g_split31;        // exact weighting by 32 x 32-bit products (see the plan)
     int prefetch_ahead;   // tile launch: prefetch the tile this many CTAs ahead into L2 (0: off)
     long long game0;
-    const void *wstage;   // weight rows per u_H (see the plan); null when wstage_block == 0
+    const void *wstage;   // weight rows per u_H (built by every fast plan)
     int wstage_block;     // bytes per u_H, a multiple of 16
 };
 
@@ -301,54 +301,15 @@ __device__ __forceinline__ void fast_round(const Acc (&x)[16], Acc *regA, Acc *r
     if constexpr (RD < L) fast_round<L, RD + 1>(x, regA, regB, regY, tid, pos);
 }
 
-// One partial score: sum over j < J = 13 - |S_L| of the weight
-// omega_s(p, |S_L| + j) (plus 1 at j = 0 when ident) times the channel
-// Y(S_L, j); wo indexes omega_s(p, |S_L|).  All loads are issued before the
-// products.  Exact path: weights are integer numerators over D_s (the
-// identity term is D_s); with g_split31 every product is two 32 x 32-bit
-// multiply-adds (y = yh 2^31 + yl), else a full 64 x 64 -> 128-bit product.
-template <typename Acc, int J>
-__device__ __forceinline__ typename GTraits<Acc>::G fast_g_entry(const FastArgs &a, const Acc *y, long long wo, int s,
-                                                                bool ident) {
-    using GT = typename GTraits<Acc>::G;
-    Acc yv[J];
-#pragma unroll
-    for (int j = 0; j < J; ++j) yv[j] = y[j];
-    if constexpr (TileTraits<Acc>::exact) {
-        long long c[J];
-#pragma unroll
-        for (int j = 0; j < J; ++j) c[j] = __ldg(a.wnum + wo + j);
-        if (ident) c[0] += __ldg(a.wden + s);
-        if (a.g_split31) {
-            long long acc_h = 0, acc_l = 0;
-#pragma unroll
-            for (int j = 0; j < J; ++j) {
-                acc_h += (long long)(int)c[j] * (int)(yv[j] >> 31);
-                acc_l += (long long)(int)c[j] * (int)(yv[j] & 0x7fffffffll);
-            }
-            return (GT)(((unsigned __int128)(__int128)acc_h) << 31) + (GT)acc_l;
-        }
-        GT acc = 0;
-#pragma unroll
-        for (int j = 0; j < J; ++j) acc += mul_wide(yv[j], c[j]);
-        return acc;
-    } else {
-        Acc acc = 0;
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-            Acc c = (sizeof(Acc) == 4) ? (Acc)__ldg(a.wf32 + wo + j) : (Acc)__ldg(a.wf64 + wo + j);
-            if (j == 0 && ident) c += (Acc)1;
-            acc += yv[j] * c;
-        }
-        return acc;
-    }
-}
-
-// Weight rows in shared memory per tile: int32 on the exact path (valid
-// when g_split31 holds: every weight plus the identity term fits), the
-// arithmetic's own type otherwise.  The plan holds the rows of every u_H;
-// a tile copies its u_H block with cp.async when it starts and waits for
-// the copy only before the ranked sums, so the copy costs no latency.
+// Weight rows in shared memory per tile, row (s, |S_L|, i) holding the
+// weights omega_s(u_H + r - i, |S_L| + j) of j = 0 .. 12 - |S_L| with the
+// identity term (1, or D_s on the exact path) at j = 0 when i = u_H and the
+// sign (-1)^(r - i) folded in, r = s - |S_L|: int32 on the exact path when
+// g_split31 holds (every weight plus the identity term fits), int64 on the
+// exact path otherwise, the arithmetic's own type on the float paths.  The
+// plan holds the rows of every u_H; a tile copies its u_H block with
+// cp.async when it starts and waits for the copy only before the ranked
+// sums, so the copy costs no latency.
 template <typename Acc>
 struct WTraits {
     using W = Acc;
@@ -418,8 +379,7 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
     const int tid = threadIdx.x;
     const In *src = reinterpret_cast<const In *>(a.v) + (game << a.d) + (tile << 12);
     const int uH = __popcll((unsigned long long)tile);
-    const bool staged = a.wstage_block > 0;
-    if (staged) {
+    {
         const char *wsrc = reinterpret_cast<const char *>(a.wstage) + (size_t)uH * a.wstage_block;
         const unsigned wdst = (unsigned)__cvta_generic_to_shared(wst);
         for (int o = tid * 16; o < a.wstage_block; o += kTileThreads * 16)
@@ -488,16 +448,15 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
     const int pos = t3 + 16 * t2;
     fast_block1<L, 0>(x, regB, pos);
     // the weight rows are read only after this barrier
-    if (staged) asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     fast_round<L, 0>(x, regA, regB, regY, tid, pos);
     // ---- partial scores G(S_L, s, i) of this tile ----
-    const int P1 = a.h + 1, Q1 = 13;
     // partial scores of a game are stored entry-major, [n_g][2^h tiles], so
     // that the combine's lanes (consecutive tiles) read consecutive addresses
     const long long ntile = 1ll << a.h;
     GT *gdst = reinterpret_cast<GT *>(a.G) + (game << a.h) * (long long)a.n_g + tile;
-    if (staged) {
+    {
         for (int g = tid; g < a.n_g; g += kTileThreads) {
             const int cb = __ldg(a.gtab + 2 * g), code = __ldg(a.gtab + 2 * g + 1);
             const int sL = code & 0xff, s = (code >> 8) & 0xff, i = code >> 16;
@@ -527,26 +486,6 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
             }
             gdst[g * ntile] = acc;
         }
-    } else
-    for (int g = tid; g < a.n_g; g += kTileThreads) {
-        const int cb = __ldg(a.gtab + 2 * g), code = __ldg(a.gtab + 2 * g + 1);
-        const int sL = code & 0xff, s = (code >> 8) & 0xff, i = code >> 16;
-        const int r = s - sL, pp = uH + r - i;
-        GT acc = 0;
-        if (i <= uH && r - i <= a.h - uH) {
-            // entries are sorted by |S_L|, so a warp almost always takes one case
-            const long long wo = ((long long)s * P1 + pp) * Q1 + sL;
-            const bool ident = (i == uH);
-            switch (sL) {
-                case 0: acc = fast_g_entry<Acc, 13>(a, regY + cb, wo, s, ident); break;
-                case 1: acc = fast_g_entry<Acc, 12>(a, regY + cb, wo, s, ident); break;
-                case 2: acc = fast_g_entry<Acc, 11>(a, regY + cb, wo, s, ident); break;
-                case 3: acc = fast_g_entry<Acc, 10>(a, regY + cb, wo, s, ident); break;
-                default: acc = fast_g_entry<Acc, 9>(a, regY + cb, wo, s, ident); break;
-            }
-            if ((r - i) & 1) acc = -acc;
-        }
-        gdst[g * ntile] = acc;
     }
     if constexpr (TileTraits<Acc>::exact) {
         if (tid == 0) a.tile_exp[(game << a.h) + tile] = a.prec_bits + 1022 - E;

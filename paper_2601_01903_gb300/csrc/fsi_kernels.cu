@@ -702,7 +702,7 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
                            cudaEvent_t ev2 = nullptr) {
     // every table a kernel of this plan will read must be in place
     const bool exact = TileTraits<Acc>::exact;
-    if (!p.d_tasks || !p.d_Y || !p.d_err || (p.fast12 && !p.d_gtab) || (p.wstage_block > 0 && !p.d_wstage) ||
+    if (!p.d_tasks || !p.d_Y || !p.d_err || (p.fast12 && !p.d_gtab) || (p.fast12 && (p.wstage_block <= 0 || !p.d_wstage)) ||
         (!p.mob_only && !p.fast12 && !p.d_trans) ||
         (exact && (!p.d_wnum || !p.d_wden || !p.d_winv || !p.d_exp)) ||
         (!exact && sizeof(Acc) == 8 && !p.d_wf64) || (!exact && sizeof(Acc) == 4 && !p.d_wf32))
