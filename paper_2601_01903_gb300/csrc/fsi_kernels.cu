@@ -180,14 +180,15 @@ __device__ __forceinline__ __int128 shfl_down_i128(__int128 v, int o) {
 // instructions only (float64 is slow on this part): the leading one of |x|
 // gives the exponent, the next 52 bits the mantissa, the rest the rounding.
 // Returns false when the result is not a normal double (the caller then
-// takes the float64 route); |x| < 2^127.
+// takes the float64 route); the magnitude is taken in unsigned arithmetic,
+// so x = -2^127 is converted too.
 __device__ __forceinline__ bool i128_scaled_to_double(__int128 x, int F, double &out) {
     if (x == 0) {
         out = 0.0;
         return true;
     }
     const unsigned long long sign = x < 0 ? (1ull << 63) : 0ull;
-    const unsigned __int128 u = x < 0 ? (unsigned __int128)(-x) : (unsigned __int128)x;
+    const unsigned __int128 u = x < 0 ? (unsigned __int128)0 - (unsigned __int128)x : (unsigned __int128)x;
     const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
     const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);  // 0 .. 127
     unsigned long long top, rest;  // |x| << lz: bits 127..64 and 63..0
