@@ -413,13 +413,15 @@ def run_configs(args, rank, world, local_rank):
                              "hbm_frac_of_measured": B * (1 << d) * elem / (ms * 1e-3) / 1e9 / peaks()[0],
                              "calls_timed": reps, "variant": "default"})
                 plan.close()
-    # the comparison variant: the same scores by the site-by-site sweep
-    for label, key, d, ell in specs[2:4]:
+    # the comparison variants: the same scores by the site-by-site sweep, and
+    # by the sweep of the precontracted operator on v
+    for (label, key, d, ell), variant in [(sp, vr) for vr in ("site", "precontract") for sp in specs[2:4]]:
         v64 = inputs(key)
         B = v64.shape[0]
         for arith in ("exact", "f32"):
             v = v64.float() if arith == "f32" else v64
-            plan = fsi.Plan(d, ell, arith, max_batch=B, site_sweep=True)
+            plan = fsi.Plan(d, ell, arith, max_batch=B, site_sweep=variant == "site",
+                            precontract=variant == "precontract")
             out = torch.empty((B, plan.n_scores), dtype=v.dtype, device=dev)
             for i in range(2):
                 plan.apply(v, out=out)
@@ -436,7 +438,9 @@ def run_configs(args, rank, world, local_rank):
             rows.append({"config": label, "index": "fsi", "arith": arith, "d": d, "ell": ell, "B": B,
                          "ms_per_call": ms, "coalitions_per_s": B * (1 << d) / (ms * 1e-3),
                          "hbm_frac_of_measured": B * (1 << d) * elem / (ms * 1e-3) / 1e9 / peaks()[0],
-                         "calls_timed": 5, "variant": "site-by-site sweep (Algorithm 1 form)",
+                         "calls_timed": 5,
+                         "variant": ("site-by-site sweep (Algorithm 1 form)" if variant == "site" else
+                                     "precontracted sweep (Section 3.5, no Moebius pass)"),
                          "tile_bits": plan.tile_bits})
             plan.close()
     if rank == 0:

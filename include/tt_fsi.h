@@ -134,6 +134,17 @@ tt_fsi_status tt_fsi_plan_create_index(int d, int ell, tt_fsi_index index, tt_fs
  */
 #define TT_FSI_PLAN_SITE_SWEEP 1u
 
+/*
+ *  TT_FSI_PLAN_PRECONTRACT: the site-by-site sweep of the precontracted
+ *    operator B_corr = A_trunc o mu (Section 3.5, Eq. B_corr): the tiles of v
+ *    are contracted without a separate Moebius pass, each site's core taking
+ *    its tau = 1 input as x[tau = 1] - x[tau = 0] (the composition with the
+ *    2 x 2 Moebius matrix); same scores as the default plan.  Implies the
+ *    site-by-site form; ignored where l >= d (the Moebius coefficients are
+ *    the scores).
+ */
+#define TT_FSI_PLAN_PRECONTRACT 2u
+
 /* As tt_fsi_plan_create_index, with option flags (0 or TT_FSI_PLAN_*). */
 tt_fsi_status tt_fsi_plan_create_ex(int d, int ell, tt_fsi_index index, tt_fsi_arith arith, int64_t max_batch,
                                     unsigned flags, tt_fsi_plan *out);

@@ -59,14 +59,17 @@ class Plan:
     ``d``-player games, for batches of up to ``max_batch`` games."""
 
     def __init__(self, d: int, ell: int, arith: str = "exact", max_batch: int = 1, index: str = "fsi",
-                 site_sweep: bool = False):
+                 site_sweep: bool = False, precontract: bool = False):
         """site_sweep: contract every tile site by site (the paper's sweep),
-        the comparison variant of the default 4-bit register groups."""
+        the comparison variant of the default 4-bit register groups;
+        precontract: the same sweep of the precontracted operator on v, with
+        the Moebius step folded into each site's core (no Moebius pass)."""
         self._lib = native.load()
         self.d, self.ell, self.arith, self.max_batch, self.index = d, ell, arith, max_batch, index
         h = ctypes.c_void_p()
         _check(self._lib.tt_fsi_plan_create_ex(d, ell, INDEX[index], ARITH[arith], max_batch,
-                                               1 if site_sweep else 0, ctypes.byref(h)), "tt_fsi_plan_create_ex")
+                                               (1 if site_sweep else 0) | (2 if precontract else 0),
+                                               ctypes.byref(h)), "tt_fsi_plan_create_ex")
         self._h = h
         self.n_scores = num_scores(d, ell)
 

@@ -60,7 +60,9 @@ struct CombineArgs {
     long long game0;
 };
 
-template <typename Acc>
+// PRE: the precontracted sweep (input v, the Moebius step of bit k fused
+// into level k); a template flag so that the plain sweep keeps its loop.
+template <typename Acc, bool PRE = false>
 __global__ void __launch_bounds__(kTileThreads) fsi_tile_kernel(TileArgs a) {
     using In = typename TileTraits<Acc>::In;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -104,8 +106,9 @@ __global__ void __launch_bounds__(kTileThreads) fsi_tile_kernel(TileArgs a) {
     }
     __syncthreads();
 
-    // Moebius transform on the b tile bits: x[T u {k}] -= x[T] for T without k.
-    for (int k = 0; k < a.b; ++k) {
+    // Moebius transform on the b tile bits: x[T u {k}] -= x[T] for T without k
+    // (skipped by the precontracted sweep, which applies it level by level).
+    for (int k = 0; k < (PRE ? 0 : a.b); ++k) {
         const int lo_mask = (1 << k) - 1;
         for (int i = tid; i < (n >> 1); i += kTileThreads) {
             int e0 = ((i >> k) << (k + 1)) | (i & lo_mask);
@@ -131,7 +134,12 @@ __global__ void __launch_bounds__(kTileThreads) fsi_tile_kernel(TileArgs a) {
                 int2 s = __ldg(tr + st);
                 Acc val = 0;
                 if (s.x >= 0) val += in[(2 * t2) * nk + s.x];
-                if (s.y >= 0) val += in[(2 * t2 + 1) * nk + s.y];
+                if (s.y >= 0) {
+                    val += in[(2 * t2 + 1) * nk + s.y];
+                    // B_corr = A_trunc o Moebius (Section 3.5): the tau_k = 1 input
+                    // of a core is x[tau_k = 1] - x[tau_k = 0]
+                    if constexpr (PRE) val -= in[(2 * t2) * nk + s.y];
+                }
                 nxt[idx] = val;
             }
             __syncthreads();
@@ -799,7 +807,10 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
                 default: fsi_tile_fast_kernel<Acc, 4><<<g1, kTileThreads, p.smem_fast, st>>>(fa); break;
             }
         } else {
-            fsi_tile_kernel<Acc><<<g1, kTileThreads, p.smem_tile, st>>>(ta);
+            if (p.precontract)
+                fsi_tile_kernel<Acc, true><<<g1, kTileThreads, p.smem_tile, st>>>(ta);
+            else
+                fsi_tile_kernel<Acc><<<g1, kTileThreads, p.smem_tile, st>>>(ta);
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_status(e);
@@ -885,12 +896,13 @@ tt_fsi_status tt_fsi_plan_create_index(int d, int ell, tt_fsi_index index, tt_fs
 
 tt_fsi_status tt_fsi_plan_create_ex(int d, int ell, tt_fsi_index index, tt_fsi_arith arith, int64_t max_batch,
                                     unsigned flags, tt_fsi_plan *out) {
-    if (!out || (flags & ~(unsigned)TT_FSI_PLAN_SITE_SWEEP)) return TT_FSI_ERR_INVALID_ARG;
+    if (!out || (flags & ~(unsigned)(TT_FSI_PLAN_SITE_SWEEP | TT_FSI_PLAN_PRECONTRACT))) return TT_FSI_ERR_INVALID_ARG;
     *out = nullptr;
     tt_fsi_plan_s *h = new (std::nothrow) tt_fsi_plan_s();
     if (!h) return TT_FSI_ERR_NO_MEMORY;
     Plan &p = h->p;
-    tt_fsi_status st = plan_build_host(p, d, ell, arith, max_batch, index, (flags & TT_FSI_PLAN_SITE_SWEEP) != 0);
+    tt_fsi_status st = plan_build_host(p, d, ell, arith, max_batch, index, (flags & TT_FSI_PLAN_SITE_SWEEP) != 0,
+                                       (flags & TT_FSI_PLAN_PRECONTRACT) != 0);
     if (st != TT_FSI_OK) {
         delete h;
         return st;
@@ -928,12 +940,16 @@ tt_fsi_status tt_fsi_plan_create_ex(int d, int ell, tt_fsi_index index, tt_fsi_a
             break;
         }
         const int smem = (int)p.smem_tile;
-        if (arith == TT_FSI_ARITH_EXACT)
+        if (arith == TT_FSI_ARITH_EXACT) {
             e = allow_max_smem(fsi_tile_kernel<long long>);
-        else if (arith == TT_FSI_ARITH_F64)
+            if (e == cudaSuccess) e = allow_max_smem(fsi_tile_kernel<long long, true>);
+        } else if (arith == TT_FSI_ARITH_F64) {
             e = allow_max_smem(fsi_tile_kernel<double>);
-        else
+            if (e == cudaSuccess) e = allow_max_smem(fsi_tile_kernel<double, true>);
+        } else {
             e = allow_max_smem(fsi_tile_kernel<float>);
+            if (e == cudaSuccess) e = allow_max_smem(fsi_tile_kernel<float, true>);
+        }
         if (e != cudaSuccess) {
             st = cuda_status(e);
             break;

@@ -145,7 +145,7 @@ void score_masks(int d, int ell, uint64_t *out) {
 }
 
 tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64_t max_batch,
-                              tt_fsi_index index, bool site_sweep) {
+                              tt_fsi_index index, bool site_sweep, bool precontract) {
     if (d < 1 || ell < 1 || max_batch < 1) return TT_FSI_ERR_INVALID_ARG;
     if (index != TT_FSI_INDEX_FSI && index != TT_FSI_INDEX_SII && index != TT_FSI_INDEX_BII &&
         index != TT_FSI_INDEX_STII)
@@ -174,8 +174,10 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
     // Eq. correction's weights depend only on |S| and |T|, so the scores of
     // the sets inside [d] are unchanged.  Otherwise: the largest b <=
     // min(d, 12) whose two ranked-sum buffers fit in shared memory.
-    // (site_sweep: always the site-by-site kernels, as a comparison variant)
-    const bool want_fast = !site_sweep && !p.mob_only && p.ell_eff <= 4;
+    // (site_sweep, precontract: always the site-by-site kernels, as comparison
+    // variants; precontract applies only where there are ranked sums)
+    const bool want_fast = !site_sweep && !precontract && !p.mob_only && p.ell_eff <= 4;
+    p.precontract = precontract && !p.mob_only;
     int b = want_fast ? kMaxTileBits : std::min(d, kMaxTileBits);
     for (;; --b) {
         if (want_fast) {

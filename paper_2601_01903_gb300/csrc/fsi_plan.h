@@ -37,6 +37,7 @@ Rational weight_rational(int ell, int s, int t);
 Rational index_weight(tt_fsi_index index, int ell, int s, int t);
 
 struct Plan {
+    bool precontract = false;  // site-by-site sweep of B_corr on v (no Moebius pass)
     int d = 0, ell = 0, ell_eff = 0;
     tt_fsi_index index = TT_FSI_INDEX_FSI;
     tt_fsi_arith arith = TT_FSI_ARITH_EXACT;
@@ -114,7 +115,8 @@ struct Plan {
 
 // Builds every host table of the plan (no CUDA calls).  Returns a status.
 tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64_t max_batch,
-                              tt_fsi_index index = TT_FSI_INDEX_FSI, bool site_sweep = false);
+                              tt_fsi_index index = TT_FSI_INDEX_FSI, bool site_sweep = false,
+                              bool precontract = false);
 
 // Scores and their order.
 int64_t num_scores(int d, int ell);

@@ -54,7 +54,7 @@ def test_unknown_plan_flag_rejected_on_host():
     import paper_2601_01903_gb300 as fsi
     lib = fsi.native.load()
     h = ctypes.c_void_p()
-    assert lib.tt_fsi_plan_create_ex(10, 2, 0, 0, 1, 2, ctypes.byref(h)) == 1
+    assert lib.tt_fsi_plan_create_ex(10, 2, 0, 0, 1, 4, ctypes.byref(h)) == 1
     assert not h.value
 
 

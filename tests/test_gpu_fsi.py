@@ -282,6 +282,24 @@ def test_site_sweep_variant_matches_oracle(oracle_mod, arith, d, ell, B):
     assert _rel_err(got, oracle_mod.fsi(v, d, ell), v) <= TOL
 
 
+@pytest.mark.parametrize("arith", ["exact", "f64", "f32"])
+@pytest.mark.parametrize("d,ell,B", [(14, 2, 3), (16, 3, 2), (9, 3, 2), (13, 4, 1), (11, 5, 2), (5, 6, 2)])
+def test_precontracted_sweep_matches_oracle(oracle_mod, arith, d, ell, B):
+    """The precontracted operator (Section 3.5) swept site by site on v
+    gives the same scores: bit for bit on the exact path (the channels are
+    the same integers), within the parity bar in float64, within the float32
+    bound in float32; l >= d keeps its Moebius pass."""
+    v = _noise_games(d, B, seed=800 + d + ell)
+    dt = torch.float32 if arith == "f32" else torch.float64
+    plan = fsi.Plan(d, ell, arith, max_batch=B, precontract=True)
+    got = plan.apply(_gpu(v, dt)).cpu().numpy().astype(np.float64)
+    plan.check()
+    assert _rel_err(got, oracle_mod.fsi(v, d, ell), v) <= (1e-4 if arith == "f32" else TOL)
+    if arith == "exact":
+        ref = fsi.Plan(d, ell, arith, max_batch=B, site_sweep=True)
+        assert np.array_equal(got, ref.apply(_gpu(v)).cpu().numpy())
+
+
 @pytest.mark.parametrize("arith", ["exact", "f32"])
 @pytest.mark.parametrize("chunk", [0, 1, 3, 7])
 @pytest.mark.parametrize("pinned", [True, False])
