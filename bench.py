@@ -376,6 +376,12 @@ def run_configs(args, rank, world, local_rank):
                 gens[name] = masked(synthetic.workload_mlp_d20())
             elif name == "d24":
                 gens[name] = masked(synthetic.workload_mlp_d24())
+            elif name == "d28":
+                # device time does not depend on the values: seeded noise,
+                # one game of 2^28 coalitions (2 GiB)
+                g = torch.Generator(device=dev)
+                g.manual_seed(28)
+                gens[name] = torch.randn((1, 1 << 28), dtype=torch.float64, device=dev, generator=g)
         return gens[name]
 
     rows = []
@@ -383,7 +389,8 @@ def run_configs(args, rank, world, local_rank):
              ("cfg2 masked MLP d=14 l=2 B=64", "d14", 14, 2),
              ("cfg3a masked MLP d=20 l=3 B=16", "d20", 20, 3),
              ("cfg3b masked MLP d=24 l=2 B=1", "d24", 24, 2),
-             ("order 4, masked MLP d=20 B=16", "d20", 20, 4)]
+             ("order 4, masked MLP d=20 B=16", "d20", 20, 4),
+             ("large d: noise game d=28 l=3 B=1", "d28", 28, 3)]
     for label, key, d, ell in specs:
         v64 = inputs(key)
         B = v64.shape[0]

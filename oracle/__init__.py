@@ -12,6 +12,11 @@ What is here:
 * ``fsi`` -- the closed form (Eq. fsi_closed with Eq. correction and
   Eq. weight), float64, Moebius by the per-player Kronecker factors and the
   correction by explicit superset enumeration (C, OpenMP over outputs).
+* ``fsi_direct`` -- listed scores straight from v: the closed form with
+  a = Moebius(v) substituted, phi(S) = sum over R of kappa(|S|, |R|, |S n R|)
+  v(R), kappa exact in rationals, v summed per (|R|, |S n R|) bin with
+  compensated sums (C).  Accurate at large d, where the float64 Moebius
+  coefficients lose digits to cancellation.
 * ``fsi_exact`` -- the same closed form in exact rational arithmetic
   (Python ``fractions``), Moebius by explicit submask sums; d <= 10.
 * ``fsi_wls`` -- the defining weighted least-squares problem (Eq. fsi_wls)
@@ -78,6 +83,8 @@ def _load():
             d, i, i64, p = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
             lib.oracle_weight.restype = d
             lib.oracle_weight.argtypes = [i, i, i]
+            lib.oracle_bin_sums.restype = None
+            lib.oracle_bin_sums.argtypes = [i, i, p, i64, p, p]
             lib.oracle_num_scores.restype = i64
             lib.oracle_num_scores.argtypes = [i, i]
             lib.oracle_score_masks.restype = i64
@@ -207,6 +214,54 @@ def fsi_at(v, d: int, ell: int, masks: Sequence[int]) -> np.ndarray:
     m = np.ascontiguousarray(np.asarray(masks, dtype=np.uint64))
     out = np.empty(m.shape[0], dtype=np.float64)
     _load().oracle_fsi_from_mobius(d, ell, _ptr(a), m.shape[0], _ptr(m), _ptr(out))
+    return out
+
+
+def direct_kernel(d: int, ell: int, s: int, r: int, q: int) -> Fraction:
+    """kappa(s, r, q): the coefficient of v(R) in phi(S) for |S| = s,
+    |R| = r, |S n R| = q.  Substituting a(T) = sum over R <= T of
+    (-1)^(|T| - |R|) v(R) into phi(S) = sum over T >= S of W(s, |T|) a(T)
+    (Eq. fsi_closed with Eq. correction: W(s, s) = 1, W(s, t) = w(s, t) of
+    Eq. weight for t > l, 0 otherwise) and counting the C(d - u, m) sets T
+    of size u + m that contain S u R (u = s + r - q) gives
+        kappa = sum over m of (-1)^(u + m - r) C(d - u, m) W(s, u + m),
+    exact in rationals."""
+    u = s + r - q
+    acc = Fraction(0)
+    for m in range(d - u + 1):
+        t = u + m
+        W = Fraction(1) if t == s else (weight_exact(ell, s, t) if t > ell else Fraction(0))
+        if W:
+            term = math.comb(d - u, m) * W
+            acc += term if (u + m - r) % 2 == 0 else -term
+    return acc
+
+
+def fsi_direct(v, d: int, ell: int, masks: Sequence[int]) -> np.ndarray:
+    """Listed scores of one game straight from v, without a Moebius
+    transform: phi(S) = sum over (r, q) of kappa(|S|, r, q) times the sum of
+    v(R) over |R| = r, |R n S| = q (compensated sums in C, then one
+    correctly rounded sum of the weighted bins).  Its error does not grow
+    with the cancellation inside the Moebius coefficients, which the
+    Moebius route (``fsi_at``) suffers at large d."""
+    v = _as_games(v, d)[0]
+    m = np.ascontiguousarray(np.asarray(masks, dtype=np.uint64))
+    nb = (d + 1) * (ell + 1)
+    bins = np.empty((m.shape[0], nb), dtype=np.float64)
+    _load().oracle_bin_sums(d, ell, _ptr(v), m.shape[0], _ptr(m), _ptr(bins))
+    kap = {}
+    out = np.empty(m.shape[0], dtype=np.float64)
+    for k in range(m.shape[0]):
+        s = _popcount(int(m[k]))
+        terms = []
+        for r in range(d + 1):
+            for q in range(min(s, r) + 1):
+                key = (s, r, q)
+                if key not in kap:
+                    kap[key] = direct_kernel(d, ell, s, r, q)
+                if kap[key]:
+                    terms.append(float(kap[key] * Fraction(float(bins[k, r * (ell + 1) + q]))))
+        out[k] = math.fsum(terms)
     return out
 
 

@@ -178,6 +178,38 @@ void oracle_fsi_from_mobius(int d, int ell, const double *a, int64_t n_masks,
 }
 
 /*
+ * For each listed coalition S (|S| <= l): the sums of v(R) over the bins
+ * (r, q) = (|R|, |R n S|), bins[k][r * (l + 1) + q], each accumulated with
+ * Neumaier's compensated summation (Neumaier 1974) so that the bin sums are
+ * accurate to a few units in the last place whatever d.  With these, a score
+ * is a short weighted sum (the direct route of the oracle, no Moebius
+ * transform).  OpenMP over the listed coalitions.
+ */
+void oracle_bin_sums(int d, int ell, const double *v, int64_t n_masks, const uint64_t *masks, double *bins)
+{
+    const uint64_t n = (uint64_t)1 << d;
+    const int nb = (d + 1) * (ell + 1);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < n_masks; ++k) {
+        const uint64_t S = masks[k];
+        double *sum = (double *)calloc((size_t)nb * 2, sizeof(double));
+        if (!sum) continue;
+        double *cmp = sum + nb;
+        for (uint64_t R = 0; R < n; ++R) {
+            const int b = popcount64(R) * (ell + 1) + popcount64(R & S);
+            const double x = v[R], t = sum[b] + x;
+            if (fabs(sum[b]) >= fabs(x))
+                cmp[b] += (sum[b] - t) + x;
+            else
+                cmp[b] += (x - t) + sum[b];
+            sum[b] = t;
+        }
+        for (int b = 0; b < nb; ++b) bins[k * nb + b] = sum[b] + cmp[b];
+        free(sum);
+    }
+}
+
+/*
  * FSI of B games of d players (v is [B, 2^d] row-major, phi is
  * [B, n_scores]): Moebius by the per-player factors, then the explicit
  * superset sums above.  Returns 0, or -1 on bad arguments / no memory.

@@ -119,6 +119,20 @@ def test_d24_order2_sampled(oracle_mod):
     assert _rel_err(got, ref, v) <= TOL
 
 
+def test_d26_order3_sampled_scores(oracle_mod):
+    """d=26, l=3, one game (2^26 float64 = 512 MiB, 2^14 tiles): sampled
+    scores of every size, with low and high players, against the oracle's
+    direct route from v (at this d the float64 Moebius route itself is off
+    by about 2e-10 of max|v| through cancellation in the coefficients)."""
+    d, ell = 26, 3
+    v = _noise_games(d, 1, seed=26)
+    got, plan = _run(v, d, ell, "exact")
+    masks = fsi.score_masks(d, ell)
+    pick = [0, 1, 2, 12, 25, 26, 27, 40, 200, 300, 351, 352, 353, 1000, 2000, 2601, len(masks) - 1]
+    ref = oracle_mod.fsi_direct(v, d, ell, [int(masks[i]) for i in pick])
+    assert _rel_err(got[0, pick], ref, v) <= TOL
+
+
 def test_sparse_games_recover_moebius_coefficients(oracle_mod):
     g = synthetic.workload_uneven(count=6, keep_m=True)
     for k in range(6):

@@ -368,3 +368,30 @@ def test_interventional_value_function_end_points_and_rows(oracle_mod):
                        rtol=0, atol=1e-14)
     assert np.allclose(oracle_mod.masked_game_interventional(mlp, x, np.repeat(bg[2:3], 3, axis=0)),
                        oracle_mod.masked_game(mlp, x, bg[2]), rtol=0, atol=1e-13)
+
+
+def test_direct_kernel_order_one_is_the_shapley_kernel(oracle_mod):
+    """At l = 1 the FSI of a single player is its Shapley value, whose
+    coefficient of v(R) is the textbook (r-1)!(d-r)!/d! when the player is in
+    R and -r!(d-r-1)!/d! when not (Shapley 1953); the empty score is v(empty)."""
+    from fractions import Fraction
+    from math import factorial
+    for d in (3, 7, 12):
+        for r in range(d + 1):
+            inside = oracle_mod.direct_kernel(d, 1, 1, r, 1) if r >= 1 else None
+            outside = oracle_mod.direct_kernel(d, 1, 1, r, 0) if r <= d - 1 else None
+            if inside is not None:
+                assert inside == Fraction(factorial(r - 1) * factorial(d - r), factorial(d))
+            if outside is not None:
+                assert outside == -Fraction(factorial(r) * factorial(d - r - 1), factorial(d))
+            assert oracle_mod.direct_kernel(d, 2, 0, r, 0) == (1 if r == 0 else 0)
+
+
+@pytest.mark.parametrize("d,ell", [(9, 2), (11, 3), (10, 4)])
+def test_direct_route_equals_closed_form(oracle_mod, d, ell):
+    """The direct route from v (coefficients kappa, compensated bin sums)
+    and the closed form through the Moebius transform agree on every score."""
+    v = np.random.default_rng(d * 100 + ell).normal(size=(1, 1 << d))
+    masks = [int(m) for m in oracle_mod.score_masks(d, ell)]
+    got = oracle_mod.fsi_direct(v, d, ell, masks)
+    assert np.max(np.abs(got - oracle_mod.fsi(v, d, ell)[0])) <= 1e-13 * np.max(np.abs(v))
