@@ -44,7 +44,7 @@ struct CUstream_st; /* cudaStream_t without the CUDA headers */
 typedef enum {
     TT_FSI_OK = 0,
     TT_FSI_ERR_INVALID_ARG = 1,   /* bad size, order, null pointer, ... */
-    TT_FSI_ERR_UNSUPPORTED = 2,   /* valid but beyond what this build handles */
+    TT_FSI_ERR_UNSUPPORTED = 2,   /* valid but beyond the sizes the library supports */
     TT_FSI_ERR_NO_MEMORY = 3,     /* a device or host allocation failed */
     TT_FSI_ERR_CUDA = 4,          /* a CUDA runtime call failed */
     TT_FSI_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */

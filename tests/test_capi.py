@@ -33,7 +33,7 @@ def test_invalid_arguments_are_statuses_not_crashes():
     assert lib.tt_fsi_plan_create(8, 0, 0, 1, ctypes.byref(h)) == 1   # l = 0
     assert lib.tt_fsi_plan_create(0, 2, 0, 1, ctypes.byref(h)) == 1   # d = 0
     assert lib.tt_fsi_plan_create(8, 2, 7, 1, ctypes.byref(h)) == 1   # bad arithmetic
-    assert lib.tt_fsi_plan_create(31, 2, 0, 1, ctypes.byref(h)) == 2  # beyond this build
+    assert lib.tt_fsi_plan_create(31, 2, 0, 1, ctypes.byref(h)) == 2  # beyond the supported sizes
     assert lib.tt_fsi_apply(None, None, 1, None, None) == 1
     assert lib.tt_fsi_score_masks(4, 2, None) == 1
     assert lib.tt_fsi_status_string(6) == b"non-finite input"
