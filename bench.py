@@ -168,13 +168,16 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def kernel_traffic():
-    """dram bytes per launch of the tile kernel from the committed ncu
-    summary, if the kernel's source files still match the ones profiled."""
+def kernel_traffic(entry=None):
+    """dram bytes per launch of the tile kernel (or of the kernel under
+    `entry` in the file) from the committed ncu summary, if the kernel's
+    source files still match the ones profiled."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             t = json.load(f)
+        if entry is not None:
+            t = t[entry]
         h = hashlib.sha256()
         for src in t["sources"]:
             with open(os.path.join(ROOT, src), "rb") as f:
@@ -594,7 +597,8 @@ def run_uneven(args, rank, world, local_rank):
         "per_game_launches_ms": ms_g, "cuda_graph_of_per_game_ms": ms_c,
         "speedup_vs_per_game": ms_g / ms_p, "speedup_vs_graph": ms_c / ms_p,
         "roofline": {"bound": "hbm", "kernel": "fsi_batch_kernel", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None},
+                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": kernel_traffic("batch") if args.arith != "f64" else None},
         "clocks": clocks.summary(),
         "gpu_launches": args.steps,
     }
