@@ -52,10 +52,6 @@ struct FastArgs {
     int *tile_exp;
     int *err;
     const int32_t *gtab;
-    const long long *wnum;
-    const long long *wden;
-    const double *wf64;
-    const float *wf32;
     int n_g;
     int d, h, ell, prec_bits, load_mask;
     int g_split31;        // exact weighting by 32 x 32-bit products (see the plan)
@@ -372,8 +368,10 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
     Acc *regB = regA + fast::regA_elems(L);          // one round's level-4 states
     Acc *regY = regB + fast::regB_elems(L);          // channels
     using WT = typename WTraits<Acc>::W;
-    WT *wst = reinterpret_cast<WT *>((reinterpret_cast<uintptr_t>(regY + fast::n_chan(L)) + 15) &
-                                     ~(uintptr_t)15);  // this tile's weight rows
+    // this tile's weight rows: the first 16-byte boundary after the channels
+    constexpr size_t kWOff =
+        ((size_t)(fast::regA_elems(L) + fast::regB_elems(L) + fast::n_chan(L)) * sizeof(Acc) + 15) & ~(size_t)15;
+    WT *wst = reinterpret_cast<WT *>(smem_raw + kWOff);
     __shared__ int s_emax;
 
     const int tid = threadIdx.x;

@@ -643,10 +643,6 @@ void free_plan_device(Plan *p) {
 FastArgs fast_args(const Plan &p) {
     FastArgs fa{};
     fa.gtab = p.d_gtab;
-    fa.wnum = p.d_wnum;
-    fa.wden = p.d_wden;
-    fa.wf64 = p.d_wf64;
-    fa.wf32 = p.d_wf32;
     fa.n_g = p.n_g;
     fa.d = p.d;
     fa.h = p.h;
