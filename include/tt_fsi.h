@@ -136,7 +136,7 @@ tt_fsi_status tt_fsi_plan_create_index(int d, int ell, tt_fsi_index index, tt_fs
 
 /*
  *  TT_FSI_PLAN_PRECONTRACT: the site-by-site sweep of the precontracted
- *    operator B_corr = A_trunc o mu (Section 3.5, Eq. B_corr): the tiles of v
+ *    operator B_corr = A_trunc o mu (Section 3.5, precontraction): the tiles of v
  *    are contracted without a separate Moebius pass, each site's core taking
  *    its tau = 1 input as x[tau = 1] - x[tau = 0] (the composition with the
  *    2 x 2 Moebius matrix); same scores as the default plan.  Implies the
