@@ -161,7 +161,8 @@ __global__ void __launch_bounds__(kTileThreads) fsi_tile_kernel(TileArgs a) {
 // Combine of the fast path: phi(S) = sum over tiles of G(S_L, s, |U_H n S_H|),
 // one warp per score, lanes over tiles.  Exact path: tile partial scores are
 // aligned to a common exponent by exact left shifts and summed in
-// wrap-around int128, then divided once by the weight denominator.
+// wrap-around int128; the sum, scaled to a double with integer instructions,
+// is multiplied once by the reciprocal of the weight denominator.
 // ----------------------------------------------------------------------------
 constexpr int kCombineFastWarps = 8;
 
