@@ -149,6 +149,23 @@ tt_fsi_status tt_fsi_plan_create_index(int d, int ell, tt_fsi_index index, tt_fs
 tt_fsi_status tt_fsi_plan_create_ex(int d, int ell, tt_fsi_index index, tt_fsi_arith arith, int64_t max_batch,
                                     unsigned flags, tt_fsi_plan *out);
 
+/*
+ * Host introspection (no device memory): the combined weights of the exact
+ * plan for (d, l, index).  A tile of 2^b coalitions (b = dims[3], the high
+ * pattern U_H of h = dims[4] bits with u_H set bits) contributes to the
+ * score of S = S_L u S_H (|S| = s, r = |S_H|, i = |U_H n S_H|)
+ *   (-1)^(r - i) sum_j [omega_s(u_H + r - i, |S_L| + j) + [i = u_H][j = 0]] Y(S_L, j),
+ * Y(S_L, j) the sum over T_L containing S_L with |T_L| = |S_L| + j of the
+ * tile's Moebius coefficients over its b low players; omega_s(p, q) =
+ * num[(s * P1 + p) * Q1 + q] / den[s] (P1 = dims[1], Q1 = dims[2],
+ * s < dims[0]) folds the weight of Eq. weight (or the index's) and the high
+ * players' Moebius step over the high players outside U_H and S_H.  dims
+ * receives 5 values; num (dims[0] * P1 * Q1 entries) and den (dims[0]) may
+ * be NULL to query the sizes first.  Returns the status plan creation would
+ * (TT_FSI_ERR_UNSUPPORTED where the exact weights do not fit).
+ */
+tt_fsi_status tt_fsi_plan_weights(int d, int ell, tt_fsi_index index, int64_t *num, int64_t *den, int32_t *dims);
+
 /* Releases a plan and its device memory (synchronizes the device first).
  * Accepts NULL. */
 void tt_fsi_plan_destroy(tt_fsi_plan plan);

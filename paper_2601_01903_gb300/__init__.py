@@ -48,6 +48,23 @@ def score_masks(d: int, ell: int) -> np.ndarray:
     return out
 
 
+def plan_weights(d: int, ell: int, index: str = "fsi"):
+    """Host introspection of the exact plan's combined weights (no GPU):
+    returns (num [S1, P1, Q1] int64, den [S1] int64, b, h) with
+    omega_s(p, q) = num[s, p, q] / den[s] (see tt_fsi_plan_weights)."""
+    lib = native.load()
+    dims = np.zeros(5, dtype=np.int32)
+    _check(lib.tt_fsi_plan_weights(d, ell, INDEX[index], None, None, ctypes.c_void_p(dims.ctypes.data)),
+           "tt_fsi_plan_weights")
+    S1, P1, Q1, b, h = (int(x) for x in dims)
+    num = np.zeros(S1 * P1 * Q1, dtype=np.int64)
+    den = np.zeros(S1, dtype=np.int64)
+    _check(lib.tt_fsi_plan_weights(d, ell, INDEX[index], ctypes.c_void_p(num.ctypes.data),
+                                   ctypes.c_void_p(den.ctypes.data), ctypes.c_void_p(dims.ctypes.data)),
+           "tt_fsi_plan_weights")
+    return num.reshape(S1, P1, Q1), den, b, h
+
+
 def _stream_ptr(stream=None):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()

@@ -458,3 +458,22 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
 }
 
 }  // namespace ttfsi
+
+// Host introspection of a plan's combined weights (no device memory).
+extern "C" tt_fsi_status tt_fsi_plan_weights(int d, int ell, tt_fsi_index index, int64_t *num, int64_t *den,
+                                             int32_t *dims) {
+    using namespace ttfsi;
+    if (!dims) return TT_FSI_ERR_INVALID_ARG;
+    Plan p;
+    const tt_fsi_status st = plan_build_host(p, d, ell, TT_FSI_ARITH_EXACT, 1, index);
+    if (st != TT_FSI_OK) return st;
+    const int S1 = (int)p.wden.size(), P1 = p.h + 1, Q1 = p.b + 1;
+    dims[0] = S1;
+    dims[1] = P1;
+    dims[2] = Q1;
+    dims[3] = p.b;
+    dims[4] = p.h;
+    if (num) std::memcpy(num, p.wnum.data(), p.wnum.size() * sizeof(int64_t));
+    if (den) std::memcpy(den, p.wden.data(), p.wden.size() * sizeof(int64_t));
+    return TT_FSI_OK;
+}
