@@ -27,7 +27,9 @@ What is here:
 * ``shapley_permutations`` -- Shapley values (Section 2.1 equation) by
   enumerating every player order; d <= 8.
 * ``interaction`` -- the other indices of Appendix A (SII, Banzhaf BII,
-  Shapley-Taylor STII) by their definitions over discrete derivatives (C).
+  Shapley-Taylor STII) by their definitions over discrete derivatives (C),
+  and k-SII (``ksii``) as the Bernoulli-number aggregation of those SII
+  scores (pure Python over the score list).
 * ``masked_game`` -- the model value function with absent features set to a
   baseline, one forward pass per coalition (C).
 * ``mpo_sweep`` -- the paper's own route (Section 3.3 MPO with Algorithm 1's
@@ -276,13 +278,52 @@ def fsi_from_mobius(a, d: int, ell: int) -> np.ndarray:
 INDEX_CODES = {"sii": 1, "bii": 2, "stii": 3}
 
 
+def bernoulli(n: int) -> List[Fraction]:
+    """Bernoulli numbers B_0 .. B_n as exact rationals, from their defining
+    recurrence sum_{j=0}^{m} C(m+1, j) B_j = 0 for m >= 1, B_0 = 1 (which
+    gives the convention B_1 = -1/2)."""
+    B = [Fraction(1)]
+    for m in range(1, n + 1):
+        B.append(-sum(math.comb(m + 1, j) * B[j] for j in range(m)) / (m + 1))
+    return B
+
+
+def ksii(v, d: int, ell: int) -> np.ndarray:
+    """k-SII of order l (Appendix A, "k-SII": higher-order SII terms are
+    aggregated into the scores of order <= l so that the scores become
+    efficient).  The paper prints no formula; the aggregation taken here is
+    the Bernoulli one of the k-SII literature,
+        I(S) = sum over T containing S with |T| <= l of B_{|T|-|S|} SII(T)
+    for 1 <= |S| <= l (B_1 = -1/2), SII(T) from ``interaction`` (the
+    Appendix A definition over discrete derivatives), and I(empty) = v(empty)
+    as for FSI, so that the non-empty scores sum to v(N) - v(empty)."""
+    if ell < 1:
+        raise ValueError("interaction order must be >= 1")
+    v = _as_games(v, d)
+    sii = interaction(v, d, ell, "sii")
+    masks = score_masks(d, ell).astype(np.int64)
+    pc = np.array([_popcount(int(m)) for m in masks])
+    B = [float(b) for b in bernoulli(min(ell, d))]
+    # M[i, j] = B_{|T_j| - |S_i|} where T_j contains S_i
+    sup = (masks[None, :] & masks[:, None]) == masks[:, None]
+    M = np.zeros((masks.shape[0], masks.shape[0]))
+    rows, cols = np.nonzero(sup)
+    M[rows, cols] = [B[pc[j] - pc[i]] for i, j in zip(rows, cols)]
+    out = sii @ M.T
+    out[:, 0] = v[:, 0]
+    return out
+
+
 def interaction(v, d: int, ell: int, index: str) -> np.ndarray:
     """Scores [B, n_scores] of the interaction index ``index`` ("fsi",
-    "sii", "bii" or "stii") of games v [B, 2^d].  FSI by its closed form
-    (``fsi``); the others by their definitions of Appendix A over discrete
-    derivatives (C, O(n_scores 2^d) per game, d <= 16 in practice)."""
+    "sii", "bii", "stii" or "ksii") of games v [B, 2^d].  FSI by its closed
+    form (``fsi``); SII, BII and STII by their definitions of Appendix A over
+    discrete derivatives (C, O(n_scores 2^d) per game, d <= 16 in practice);
+    k-SII by ``ksii``."""
     if index == "fsi":
         return fsi(v, d, ell)
+    if index == "ksii":
+        return ksii(v, d, ell)
     if ell < 1:
         raise ValueError("interaction order must be >= 1")
     v = _as_games(v, d)

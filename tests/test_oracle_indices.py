@@ -12,7 +12,10 @@ mathematics, not against its own formula:
   over all player orders);
 * STII is efficient: its scores of the non-empty S sum to v(N) - v(empty);
 * the Moebius form the CUDA path evaluates, sum over T containing S of
-  W(|S|, |T|) a(T), equals the definition on random games.
+  W(|S|, |T|) a(T), equals the definition on random games;
+* k-SII (given in Appendix A by its purpose and its efficiency only): the
+  hand-derived values of tests/golden/ksii_cases.json, efficiency, order 1
+  = Shapley value, top order = SII, exact recovery of l-additive games.
 """
 from fractions import Fraction
 from math import comb
@@ -95,6 +98,16 @@ def _mobius_form(a, d, ell, index):
                 w = Fraction(1, t - s + 1)
             elif index == "bii":
                 w = Fraction(1, 2 ** (t - s))
+            elif index == "ksii":
+                # W(s, s) = 1; 0 for s < t <= l (the Bernoulli sums cancel);
+                # sum_j C(t-s, j) B_j / (t-s-j+1) over j <= l - s for t > l
+                B = oracle_mod_bernoulli(ell)
+                if t == s:
+                    w = Fraction(1)
+                elif s == 0 or t <= ell:
+                    w = Fraction(0)
+                else:
+                    w = sum(comb(t - s, j) * B[j] / (t - s - j + 1) for j in range(ell - s + 1))
             else:
                 w = Fraction(int(T == S)) if s < ell else Fraction(1, comb(t, ell))
             acc += w * Fraction(a[T])
@@ -102,7 +115,12 @@ def _mobius_form(a, d, ell, index):
     return dict(out)
 
 
-@pytest.mark.parametrize("index", ["sii", "bii", "stii"])
+def oracle_mod_bernoulli(n):
+    import oracle
+    return oracle.bernoulli(n)
+
+
+@pytest.mark.parametrize("index", ["sii", "bii", "stii", "ksii"])
 def test_definition_equals_mobius_form(oracle_mod, index):
     d, ell = 6, 3
     v = np.random.default_rng(11).normal(size=1 << d)
@@ -116,3 +134,71 @@ def test_definition_equals_mobius_form(oracle_mod, index):
 def test_fsi_route_is_the_closed_form(oracle_mod):
     v = np.random.default_rng(5).normal(size=(2, 1 << 7))
     assert np.array_equal(oracle_mod.interaction(v, 7, 2, "fsi"), oracle_mod.fsi(v, 7, 2))
+
+
+# --------------------------------------------------------------------------
+# k-SII (Appendix A): pinned by hand-derived unanimity values, the
+# efficiency the paper states for it, its reductions to the Shapley value
+# (order 1) and to SII (top order), and exact recovery of l-additive games
+# --------------------------------------------------------------------------
+
+def test_bernoulli_numbers_are_the_textbook_values(oracle_mod):
+    B = oracle_mod.bernoulli(8)
+    assert B == [Fraction(1), Fraction(-1, 2), Fraction(1, 6), 0, Fraction(-1, 30), 0, Fraction(1, 42), 0,
+                 Fraction(-1, 30)]
+
+
+def test_ksii_golden_cases(oracle_mod):
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "ksii_cases.json")) as f:
+        cases = json.load(f)
+    for c in cases:
+        d, ell = c["d"], c["ell"]
+        v = np.array([float(Fraction(x)) for x in c["v"]])
+        want = np.array([float(Fraction(x)) for x in c["phi"]])
+        got = oracle_mod.interaction(v, d, ell, "ksii")[0]
+        assert np.max(np.abs(got - want)) < 1e-14, c["name"]
+        # the fixtures themselves satisfy the efficiency the paper states
+        assert sum(Fraction(x) for x in c["phi"][1:]) == Fraction(c["v"][-1]) - Fraction(c["v"][0])
+
+
+@pytest.mark.parametrize("d,ell", [(6, 2), (8, 3), (7, 4), (5, 5), (9, 1)])
+def test_ksii_is_efficient(oracle_mod, d, ell):
+    v = np.random.default_rng(d * 13 + ell).normal(size=(2, 1 << d))
+    got = oracle_mod.interaction(v, d, ell, "ksii")
+    assert np.array_equal(got[:, 0], v[:, 0])
+    assert np.max(np.abs(got[:, 1:].sum(axis=1) - (v[:, -1] - v[:, 0]))) < 1e-11
+
+
+def test_ksii_order_one_is_shapley_value(oracle_mod):
+    d = 7
+    v = np.random.default_rng(17).normal(size=1 << d)
+    sv = oracle_mod.shapley_permutations(v, d)
+    got = oracle_mod.interaction(v, d, 1, "ksii")[0]
+    assert np.max(np.abs(got[1:] - sv)) < 1e-12
+
+
+def test_ksii_top_order_is_sii(oracle_mod):
+    d, ell = 7, 3
+    v = np.random.default_rng(19).normal(size=1 << d)
+    got = oracle_mod.interaction(v, d, ell, "ksii")[0]
+    sii = oracle_mod.interaction(v, d, ell, "sii")[0]
+    top = [k for k, S in enumerate(oracle_mod.score_masks(d, ell)) if _pc(S) == ell]
+    assert np.array_equal(got[top], sii[top])
+
+
+@pytest.mark.parametrize("ell", [2, 3])
+def test_ksii_recovers_l_additive_games(oracle_mod, ell):
+    """A game whose Moebius coefficients vanish above order l keeps them as
+    its k-SII scores (the Bernoulli sums cancel every lower-order term)."""
+    d = 7
+    rng = np.random.default_rng(23 + ell)
+    m = np.zeros(1 << d)
+    for T in range(1, 1 << d):
+        if _pc(T) <= ell:
+            m[T] = rng.normal()
+    v = np.array([sum(m[R] for R in range(1 << d) if (R & T) == R) for T in range(1 << d)])
+    got = oracle_mod.interaction(v, d, ell, "ksii")[0]
+    want = m[oracle_mod.score_masks(d, ell).astype(np.int64)]
+    assert np.max(np.abs(got - want)) < 1e-12
