@@ -83,13 +83,21 @@ typedef enum {
  *                     weights); W = 2^-(|T| - |S|).
  *  TT_FSI_INDEX_STII  Shapley-Taylor index of order l (Appendix A):
  *                     a(S) for |S| < l; W = 1 / C(|T|, l) for |S| = l.
+ *  TT_FSI_INDEX_KSII  k-SII of order l (Appendix A: higher-order SII terms
+ *                     aggregated so that the scores are efficient), read as
+ *                     the Bernoulli aggregation sum_{T >= S, |T| <= l}
+ *                     B_{|T|-|S|} SII(T) (B_1 = -1/2); in Moebius form
+ *                     W = 0 for |S| < |T| <= l and
+ *                     W = sum_{j <= l-|S|} C(|T|-|S|, j) B_j / (|T|-|S|-j+1)
+ *                     for |T| > l; score 0 (the empty set) is v(empty).
  * SII and BII do not depend on l; l only bounds the scored sets |S| <= l.
  */
 typedef enum {
     TT_FSI_INDEX_FSI = 0,
     TT_FSI_INDEX_SII = 1,
     TT_FSI_INDEX_BII = 2,
-    TT_FSI_INDEX_STII = 3
+    TT_FSI_INDEX_STII = 3,
+    TT_FSI_INDEX_KSII = 4
 } tt_fsi_index;
 
 /* Opaque plan: everything that depends only on (d, l, arithmetic) --
@@ -218,6 +226,21 @@ tt_fsi_status tt_fsi_plan_set_host_chunk(tt_fsi_plan plan, int64_t games);
 tt_fsi_status tt_fsi_plan_profile(tt_fsi_plan plan, int enable);
 tt_fsi_status tt_fsi_plan_profile_read(tt_fsi_plan plan, double *ms_tile, double *ms_combine,
                                        int64_t *n_calls);
+
+/*
+ * Arithmetic throughput microbenchmark (measurement support, not part of the
+ * FSI path): one launch of `blocks` CTAs of 256 threads, each thread running
+ * 8 independent dependency chains for iters x 16 steps of one operation:
+ *   kind 0: float64 add          kind 1: float64 fused multiply-add
+ *   kind 2: 32-bit integer add   kind 3: 64-bit integer add
+ * *ops_per_launch (host) receives the number of operations the launch
+ * performs; timing it with events on `stream` gives the pipe's rate, the
+ * roofline of the float64 arithmetic (TT_FSI_ARITH_F64: its tile stage is
+ * float64 adds and multiply-adds).  out_dev (device, blocks x 256 doubles)
+ * is written only to keep the chains alive.  Asynchronous.
+ */
+tt_fsi_status tt_fsi_peak_launch(int kind, int blocks, int iters, double *out_dev, int64_t *ops_per_launch,
+                                 struct CUstream_st *stream);
 
 /*
  * Batches of uneven games.  Game g has d players and order l and lives at

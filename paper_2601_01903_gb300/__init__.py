@@ -15,7 +15,7 @@ from . import native
 
 ARITH = {"exact": 0, "f64": 1, "f32": 2}
 # interaction indices (tt_fsi_index)
-INDEX = {"fsi": 0, "sii": 1, "bii": 2, "stii": 3}
+INDEX = {"fsi": 0, "sii": 1, "bii": 2, "stii": 3, "ksii": 4}
 STATUS = {
     0: "ok", 1: "invalid argument", 2: "unsupported", 3: "out of memory", 4: "CUDA error",
     5: "device wait timed out", 6: "non-finite input", 7: "self-check failed",
@@ -173,8 +173,8 @@ class Plan:
 
 
 def fsi(v, d: int, ell: int, arith: str = "exact", index: str = "fsi"):
-    """One-shot interaction scores (FSI by default; index "sii", "bii" or
-    "stii" for the other indices) of v [B, 2^d] (CUDA tensor)."""
+    """One-shot interaction scores (FSI by default; index "sii", "bii",
+    "stii" or "ksii" for the other indices) of v [B, 2^d] (CUDA tensor)."""
     B = 1 if v.dim() == 1 else v.shape[0]
     p = Plan(d, ell, arith, max_batch=max(1, B), index=index)
     try:

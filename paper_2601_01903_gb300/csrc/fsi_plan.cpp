@@ -106,9 +106,38 @@ Rational weight_rational(int ell, int s, int t) {
     return r;
 }
 
+// Bernoulli numbers B_0 .. B_n (B_1 = -1/2) from sum_{j<=m} C(m+1, j) B_j = 0.
+const std::vector<Rational> &bernoulli_table() {
+    static const std::vector<Rational> tab = [] {
+        const Pascal &C = pascal();
+        std::vector<Rational> B(1, rat_make(1, 1));
+        for (int m = 1; m <= 30; ++m) {
+            Rational acc;
+            for (int j = 0; j < m; ++j) acc = rat_add(acc, rat_mul(rat_make(C(m + 1, j), 1), B[j]));
+            B.push_back(rat_mul(acc, rat_make(-1, m + 1)));
+        }
+        return B;
+    }();
+    return tab;
+}
+
 Rational index_weight(tt_fsi_index index, int ell, int s, int t) {
     if (t <= s || s < 0) return Rational{};
     switch (index) {
+        case TT_FSI_INDEX_KSII: {
+            // Moebius form of the Bernoulli aggregation of SII: a superset T
+            // of S reaches S through every T' with S <= T' <= T, |T'| <= l,
+            // with B_{|T'|-s} / (t - |T'| + 1); the sums vanish for t <= l
+            if (s == 0 || t <= ell) return Rational{};
+            const Pascal &C = pascal();
+            const std::vector<Rational> &B = bernoulli_table();
+            Rational acc;
+            for (int j = 0; j <= std::min(ell - s, (int)B.size() - 1); ++j) {
+                if (B[j].num == 0) continue;
+                acc = rat_add(acc, rat_mul(B[j], rat_make(C(t - s, j), (__int128)(t - s - j + 1))));
+            }
+            return acc;
+        }
         case TT_FSI_INDEX_FSI: return weight_rational(ell, s, t);
         case TT_FSI_INDEX_SII: return rat_make(1, (__int128)(t - s + 1));
         case TT_FSI_INDEX_BII: return rat_make(1, (__int128)1 << (t - s));
@@ -148,7 +177,7 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
                               tt_fsi_index index, bool site_sweep, bool precontract) {
     if (d < 1 || ell < 1 || max_batch < 1) return TT_FSI_ERR_INVALID_ARG;
     if (index != TT_FSI_INDEX_FSI && index != TT_FSI_INDEX_SII && index != TT_FSI_INDEX_BII &&
-        index != TT_FSI_INDEX_STII)
+        index != TT_FSI_INDEX_STII && index != TT_FSI_INDEX_KSII)
         return TT_FSI_ERR_INVALID_ARG;
     if (arith != TT_FSI_ARITH_EXACT && arith != TT_FSI_ARITH_F64 && arith != TT_FSI_ARITH_F32)
         return TT_FSI_ERR_INVALID_ARG;
@@ -159,10 +188,10 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
     p.index = index;
     p.arith = arith;
     p.max_batch = max_batch;
-    // With l >= d, FSI and STII leave every Moebius coefficient in place
+    // With l >= d, FSI, STII and k-SII leave every Moebius coefficient in place
     // (no superset has more than d >= l players); SII and BII still sum
     // over supersets.
-    p.mob_only = ell >= d && (index == TT_FSI_INDEX_FSI || index == TT_FSI_INDEX_STII);
+    p.mob_only = ell >= d && (index == TT_FSI_INDEX_FSI || index == TT_FSI_INDEX_STII || index == TT_FSI_INDEX_KSII);
     p.n_out = num_scores(d, ell);
     const size_t elem = (arith == TT_FSI_ARITH_F32) ? 4 : 8;
     const size_t smem_budget = 224 * 1024;  // 227 KB opt-in per CTA, minus static

@@ -1,6 +1,6 @@
 """Parity of the CUDA path for the other interaction indices (SII, Banzhaf
-BII, Shapley-Taylor STII) against the oracle's definitions over discrete
-derivatives (needs a GB300).  Same bar as FSI: max |phi_gpu - phi_oracle| /
+BII, Shapley-Taylor STII, k-SII) against the oracle's definitions over
+discrete derivatives (k-SII: their Bernoulli aggregation) (needs a GB300).  Same bar as FSI: max |phi_gpu - phi_oracle| /
 max |v| <= 1e-10 for the exact and the float64 arithmetic."""
 import numpy as np
 import pytest
@@ -12,7 +12,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-10
-INDICES = ["sii", "bii", "stii"]
+INDICES = ["sii", "bii", "stii", "ksii"]
 
 
 def _games(d, B, seed):
@@ -51,7 +51,7 @@ def test_index_matches_definition(oracle_mod, arith, index, d, ell, B):
 @pytest.mark.parametrize("d,ell", [(4, 6), (3, 3), (7, 7), (9, 12)])
 def test_order_at_least_d(oracle_mod, index, d, ell):
     """l >= d: every subset is scored; SII and BII still sum over supersets,
-    STII (like FSI) returns the Moebius coefficients."""
+    STII and k-SII (like FSI) return the Moebius coefficients."""
     v = _games(d, 2, d + ell)
     got, _ = _run(v, d, ell, "exact", index)
     ref = oracle_mod.interaction(v, d, ell, index)
@@ -90,3 +90,15 @@ def test_unknown_index_is_rejected():
     import ctypes
     h = ctypes.c_void_p()
     assert lib.tt_fsi_plan_create_index(10, 2, 7, 0, 1, ctypes.byref(h)) == 1
+
+
+@pytest.mark.parametrize("arith", ["exact", "f64"])
+def test_ksii_masked_mlp_d20_order3(oracle_mod, arith):
+    """k-SII at the headline size (d = 20, l = 3) on a masked-MLP game:
+    every score against the oracle, and the efficiency the paper states."""
+    w = synthetic.workload_mlp_d20()
+    v = oracle_mod.masked_game(w.mlp, w.x[3], w.baseline).reshape(1, -1)
+    got, _ = _run(v, 20, 3, arith, "ksii")
+    ref = oracle_mod.interaction(v, 20, 3, "ksii")
+    assert _err(got, ref, v) <= TOL
+    assert abs(got[0, 1:].sum() - (v[0, -1] - v[0, 0])) <= 1e-9 * np.abs(v).max()

@@ -66,6 +66,7 @@ def _rebuilt_scores(v, d, ell, index):
     (10, 2, "fsi"),    # fewer players than a tile: null-player padding, h = 0
     (13, 2, "fsi"), (14, 3, "fsi"), (15, 1, "fsi"), (13, 4, "fsi"),
     (14, 2, "sii"), (14, 2, "bii"), (13, 3, "stii"),
+    (14, 3, "ksii"), (13, 2, "ksii"), (12, 4, "ksii"), (15, 1, "ksii"),
 ])
 def test_tile_decomposition_with_plan_weights_equals_oracle(oracle_mod, d, ell, index):
     v = np.random.default_rng(d * 31 + ell).integers(-3, 4, size=1 << d).astype(np.float64)
