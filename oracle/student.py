@@ -118,6 +118,47 @@ def loss_and_grads(params, x, labels, target, v_empty, d, H, n_out, emulate_bf16
     return loss, grads
 
 
+def grad_magnitudes(params, x, labels, target, v_empty, d, H, n_out):
+    """Per-entry scale for comparing GPU gradients with ``loss_and_grads``:
+    the same backward pass with every sum replaced by the root of the sum of
+    its squared terms (BF16 rounding points kept), each intermediate carried
+    as that root-sum-square scale.  Changing one rounded operand by a
+    relative 2^-8 (one BF16 ulp) changes one term of each sum it feeds, so it
+    moves gradient k by at most 2^-8 times this scale; FP32 accumulation in
+    another order moves it by far less.  Element-wise tolerances are
+    multiples of 2^-8 times this value."""
+    f = forward(params, x, d, H, n_out, emulate_bf16=True)
+    B = f["Y"].shape[0]
+    phi = project(f["Y"], target, v_empty)
+    rY = np.sqrt(f["A2"] ** 2 @ f["W3"].T ** 2 + unpack(params, d, H, n_out)["b3"] ** 2)
+    # |d loss / d Y| and the scale of its changes: the error, plus the
+    # output scale (a flip in the forward pass moves Y by 2^-8 of it)
+    e = np.abs(phi - labels) + rY
+    g = 2.0 * e / (B * n_out)
+    dY = np.zeros_like(g)
+    dY[:, 1:] = np.sqrt(g[:, 1:] ** 2 + (g[:, 1:] ** 2).mean(axis=1, keepdims=True))
+    sq = lambda a: np.asarray(a, dtype=np.float64) ** 2
+    gp2, gp1 = np.abs(gelu_grad(f["Z2"])), np.abs(gelu_grad(f["Z1"]))
+    mW3 = np.sqrt(sq(dY).T @ sq(f["A2"]))
+    mb3 = np.sqrt(sq(dY).sum(axis=0))
+    dH2 = np.sqrt(sq(dY) @ sq(f["W3"])) * gp2
+    mW2 = np.sqrt(sq(dH2).T @ sq(f["A1"]))
+    mb2 = np.sqrt(sq(dH2).sum(axis=0))
+    dH1 = np.sqrt(sq(dH2) @ sq(f["W2"])) * gp1
+    mW1 = np.sqrt(sq(dH1).T @ sq(f["X"]))
+    mb1 = np.sqrt(sq(dH1).sum(axis=0))
+    return pack(dict(W1=mW1, b1=mb1, W2=mW2, b2=mb2, W3=mW3, b3=mb3))
+
+
+def output_magnitudes(params, x, d, H, n_out):
+    """Per-entry root-sum-square scale of the raw outputs,
+    sqrt(A2^2 (W3^2)^T + b3^2) (BF16 rounding points kept), the scale of
+    element-wise tolerances on forward passes (see grad_magnitudes)."""
+    f = forward(params, x, d, H, n_out, emulate_bf16=True)
+    P = unpack(params, d, H, n_out)
+    return np.sqrt(f["A2"] ** 2 @ (f["W3"] ** 2).T + P["b3"] ** 2)
+
+
 def adam_step(p, m, v, g, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam update at step t (1-based); returns new (p, m, v)."""
     m = beta1 * m + (1 - beta1) * g

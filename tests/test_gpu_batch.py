@@ -54,6 +54,32 @@ def test_uneven_batch_all_paths_match_oracle(oracle_mod):
     assert np.array_equal(outs["apply"], outs["apply_graph"])
 
 
+_FULL = {}
+
+
+@pytest.mark.parametrize("arith", ["exact", "f64"])
+def test_uneven_1024_workload_every_game_matches_oracle(oracle_mod, arith):
+    """The whole batched workload (1024 Moebius-sparse games, d in 10..20,
+    l in 1..3, one persistent launch): every score of every game against
+    the oracle, in both arithmetics, and efficiency on every game."""
+    if "g" not in _FULL:
+        g = synthetic.workload_uneven()
+        _FULL["g"] = (g, _oracle_all(oracle_mod, g))
+    g, ref = _FULL["g"]
+    b = fsi.Batch.from_ragged(g, arith=arith)
+    phi = torch.full((g.n_phi,), np.nan, dtype=torch.float64, device="cuda")
+    b.apply(torch.as_tensor(g.v, device="cuda"), phi)
+    b.check()
+    got = phi.cpu().numpy()
+    _check_per_game(g, got, ref)
+    for k in range(len(g.d)):
+        d = int(g.d[k])
+        v = g.v[g.v_off[k]:g.v_off[k] + (1 << d)]
+        po = int(g.phi_off[k])
+        n = fsi.num_scores(d, int(g.ell[k]))
+        assert abs(got[po + 1:po + n].sum() - (v[-1] - v[0])) <= 1e-9 * max(np.abs(v).max(), 1e-300)
+
+
 def test_mixed_batch_with_games_off_the_fast_path(oracle_mod):
     games, vs, off, poff = [], [], 0, 0
     specs = [(12, 3), (5, 5), (9, 4), (14, 2), (3, 1), (13, 13), (16, 1), (11, 5), (15, 4)]

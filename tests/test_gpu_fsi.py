@@ -92,31 +92,60 @@ def test_masked_mlp_d14_batch64(oracle_mod):
     assert _rel_err(got32, ref, v) <= 1e-3
 
 
-def test_masked_mlp_d20_order3(oracle_mod):
-    """d=20, l=3: two instances of the 20-128-128-1 MLP game (oracle-made
-    value vectors) batched with 14 white-noise games, 16 games in all."""
-    w = synthetic.workload_mlp_d20()
-    v = np.empty((16, 1 << 20))
-    for i in range(2):
-        v[i] = oracle_mod.masked_game(w.mlp, w.x[i], w.baseline)
-    v[2:] = _noise_games(20, 14, seed=20)
-    got, _ = _run(v, 20, 3, "exact")
-    ref = np.stack([oracle_mod.fsi(v[i], 20, 3)[0] for i in (0, 1, 2, 15)])
-    sel = got[[0, 1, 2, 15]]
-    for k in range(4):
-        assert _rel_err(sel[k], ref[k], v[[0, 1, 2, 15][k]]) <= TOL
-    # efficiency on every game of the batch
+_CACHE = {}
+
+
+def _d20_batch(oracle_mod):
+    """The d = 20, l = 3 batch: two instances of the 20-128-128-1 MLP game
+    (oracle-made value vectors) and 14 white-noise games, with the oracle's
+    scores of all 16 (computed once per session)."""
+    if "d20" not in _CACHE:
+        w = synthetic.workload_mlp_d20()
+        v = np.empty((16, 1 << 20))
+        for i in range(2):
+            v[i] = oracle_mod.masked_game(w.mlp, w.x[i], w.baseline)
+        v[2:] = _noise_games(20, 14, seed=20)
+        _CACHE["d20"] = (v, oracle_mod.fsi(v, 20, 3))
+    return _CACHE["d20"]
+
+
+@pytest.mark.parametrize("arith", ["exact", "f64"])
+def test_masked_mlp_d20_order3(oracle_mod, arith):
+    """d=20, l=3, 16 games in one call (the headline batch size): every
+    score of every game against the oracle, and efficiency on every game."""
+    v, ref = _d20_batch(oracle_mod)
+    got, _ = _run(v, 20, 3, arith)
+    assert got.shape == ref.shape == (16, 1351)
+    for k in range(16):
+        assert _rel_err(got[k], ref[k], v[k]) <= TOL, (arith, k)
     eff = got[:, 1:].sum(axis=1) - (v[:, -1] - v[:, 0])
     assert np.max(np.abs(eff) / np.abs(v).max(axis=1)) < 1e-9
 
 
-def test_d24_order2_sampled(oracle_mod):
+@pytest.mark.parametrize("arith", ["exact", "f64"])
+def test_d24_order2_sampled(oracle_mod, arith):
     """d=24, l=2, one game (2^24 float64 = 128 MiB): every score against the
-    oracle's explicit superset sums."""
-    v = _noise_games(24, 1, seed=24)
-    got, plan = _run(v, 24, 2, "exact")
-    ref = oracle_mod.fsi(v, 24, 2)
+    oracle's explicit superset sums, and efficiency."""
+    if "d24" not in _CACHE:
+        v = _noise_games(24, 1, seed=24)
+        _CACHE["d24"] = (v, oracle_mod.fsi(v, 24, 2))
+    v, ref = _CACHE["d24"]
+    got, plan = _run(v, 24, 2, arith)
     assert _rel_err(got, ref, v) <= TOL
+    assert abs(got[0, 1:].sum() - (v[0, -1] - v[0, 0])) <= 1e-9 * np.abs(v).max()
+
+
+@pytest.mark.parametrize("arith", ["exact", "f64"])
+def test_teacher_games_d16_order2(oracle_mod, arith):
+    """d=16, l=2 on 8 instances of the explainer's teacher (16-128-128-1
+    MLP, AR(1) inputs): the exact transform that labels the student."""
+    mlp = synthetic.workload_student_teacher()
+    x = synthetic.student_instances(8)
+    v = np.stack([oracle_mod.masked_game(mlp, x[i], np.zeros(16)) for i in range(8)])
+    got, _ = _run(v, 16, 2, arith)
+    ref = oracle_mod.fsi(v, 16, 2)
+    for k in range(8):
+        assert _rel_err(got[k], ref[k], v[k]) <= TOL, (arith, k)
 
 
 def test_d26_order3_sampled_scores(oracle_mod):

@@ -28,6 +28,25 @@ def _dev(a):
     return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
 
 
+# Element-wise tolerance of GPU results against the BF16-emulating oracle.
+# The GPU rounds the same operands to BF16 but accumulates in FP32 in another
+# order; an FP32 value that lands within a few FP32 ulps of a BF16 rounding
+# boundary can round to the neighbouring BF16 value (a relative change of
+# 2^-8 in that one operand).  One such flip moves an entry by at most 2^-8
+# times its root-sum-square scale (oracle.student.grad_magnitudes and
+# output_magnitudes: each sum along the entry's chain replaced by the root of
+# its summed squared terms, about the size of the entry itself); FP32
+# accumulation moves it by far less.  The bound allows four flips' worth.  A
+# wrong index, sign or dropped term moves an entry by about its own size,
+# i.e. by about 2^8 / 4 = 64 times the bound.
+FLIP = 4 * 2.0 ** -8
+
+
+def _elementwise(got, ref, mag, name):
+    bad = np.abs(got - ref) > FLIP * mag + 1e-30
+    assert not bad.any(), (name, int(bad.sum()), float(np.max(np.abs(got - ref) / (mag + 1e-30))))
+
+
 def test_gradients_match_oracle_with_bf16_rounding():
     d, H, n_out, B = 16, 64, 137, 256
     params, x, labels, target, v0 = _case(d, H, n_out, B)
@@ -35,17 +54,16 @@ def test_gradients_match_oracle_with_bf16_rounding():
     loss = s.gradients(_dev(x), _dev(labels), _dev(target), v0)
     s.check()
     g = s.grads().astype(np.float64)
-    ref_loss, ref = so.loss_and_grads(params.astype(np.float64), x, labels, target, v0, d, H, n_out,
-                                      emulate_bf16=True)
+    p64 = params.astype(np.float64)
+    ref_loss, ref = so.loss_and_grads(p64, x, labels, target, v0, d, H, n_out, emulate_bf16=True)
+    mag = so.grad_magnitudes(p64, x, labels, target, v0, d, H, n_out)
     assert abs(loss.item() - ref_loss) <= 1e-4 * abs(ref_loss)
-    rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
-    cos = float(g @ ref / (np.linalg.norm(g) * np.linalg.norm(ref)))
-    assert rel < 2e-2 and cos > 0.9998, (rel, cos)
-    # per tensor as well
     o = 0
     for name, n in (("W1", H * d), ("b1", H), ("W2", H * H), ("b2", H), ("W3", n_out * H), ("b3", n_out)):
-        r = np.linalg.norm(g[o:o + n] - ref[o:o + n]) / max(np.linalg.norm(ref[o:o + n]), 1e-30)
-        assert r < 3e-2, (name, r)
+        gs, rs, ms = g[o:o + n], ref[o:o + n], mag[o:o + n]
+        _elementwise(gs, rs, ms, name)
+        # whole tensor: a few BF16 flips at most
+        assert np.linalg.norm(gs - rs) <= 1e-2 * np.linalg.norm(rs), name
         o += n
 
 
@@ -68,7 +86,12 @@ def test_adam_step_and_projection_match_oracle():
     assert np.max(np.abs(phi[:, 1:].sum(axis=1) - target)) < 1e-3 * max(1.0, np.abs(target).max())
     f = so.forward(p1.astype(np.float64), x, d, H, n_out, emulate_bf16=True)
     ref = so.project(f["Y"], target, v0)
-    assert np.max(np.abs(phi - ref)) < 2e-2 * np.abs(ref).max()
+    # element-wise: the projection shifts every non-empty score by the mean
+    # residual, so its scale is the raw outputs' plus their mean
+    mag = so.output_magnitudes(p1.astype(np.float64), x, d, H, n_out)
+    mag[:, 1:] += mag[:, 1:].mean(axis=1, keepdims=True)
+    mag[:, 0] = 0.0
+    _elementwise(phi, ref, mag + 1e-6 * np.abs(target)[:, None], "projected outputs")
 
 
 def test_checkpoint_resume_is_bitwise(tmp_path):

@@ -71,3 +71,51 @@ def test_surrogate_matches_definition():
     coal = np.array([[0, 1, 3, 7, 6]], dtype=np.uint64)
     g = so.surrogate(phi, masks, coal)
     assert np.allclose(g, [[0.5, 1.5, 3.6, 7.1, 5.8]])
+
+
+def test_gradient_scale_separates_rounding_from_mistakes():
+    """The element-wise bound used against the GPU (4 BF16 ulps of the
+    root-sum-square scale) holds for the same arithmetic done with FP32
+    accumulation and perturbed GELU values (as on the GPU), and fails for a
+    planted mistake: two rows of the W3 gradient swapped, one b3 entry
+    dropped from its sum, one W1 entry with its sign flipped."""
+    from paper_2601_01903_gb300 import student as st
+    d, H, n_out, B = 16, 64, 137, 256
+    params = st.init_params(d, H, n_out, 1).astype(np.float64)
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(B, d)).astype(np.float32)
+    labels = (rng.normal(size=(B, n_out)) * 0.1).astype(np.float32)
+    target = rng.normal(size=B).astype(np.float32)
+    _, ref = so.loss_and_grads(params, x, labels, target, 0.2, d, H, n_out, emulate_bf16=True)
+    mag = so.grad_magnitudes(params, x, labels, target, 0.2, d, H, n_out)
+    # FP32 accumulation of BF16 operands, GELU perturbed by 1e-7 relative
+    f32, r = np.float32, (lambda a: so.bf16_round(a).astype(np.float32))
+    P = so.unpack(params, d, H, n_out)
+    X, W1, W2, W3 = r(x), r(P["W1"]), r(P["W2"]), r(P["W3"])
+    Z1 = (X @ W1.T).astype(f32) + P["b1"].astype(f32)
+    A1 = r(so.gelu(Z1.astype(np.float64)) * (1 + 1e-7 * rng.normal(size=Z1.shape)))
+    Z2 = (A1 @ W2.T).astype(f32) + P["b2"].astype(f32)
+    A2 = r(so.gelu(Z2.astype(np.float64)) * (1 + 1e-7 * rng.normal(size=Z2.shape)))
+    Y = (A2 @ W3.T).astype(f32) + P["b3"].astype(f32)
+    err = so.project(Y.astype(np.float64), target, 0.2).astype(f32) - labels
+    g = 2 * err / (B * n_out)
+    dY = np.zeros_like(g)
+    dY[:, 1:] = g[:, 1:] - g[:, 1:].mean(axis=1, keepdims=True)
+    dH2 = (r(dY) @ W3) * so.gelu_grad(Z2.astype(np.float64)).astype(f32)
+    dH1 = (r(dH2) @ W2) * so.gelu_grad(Z1.astype(np.float64)).astype(f32)
+    got = so.pack(dict(W1=r(dH1).T @ X, b1=dH1.sum(0), W2=r(dH2).T @ A1, b2=dH2.sum(0),
+                       W3=r(dY).T @ A2, b3=dY.sum(0)))
+    bound = 4 * 2.0 ** -8 * mag
+    assert np.all(np.abs(got - ref) <= bound)
+    o3 = H * d + H + H * H + H
+    ob3 = o3 + n_out * H
+    swapped = got.copy()
+    swapped[o3 + 5 * H:o3 + 6 * H], swapped[o3 + 9 * H:o3 + 10 * H] = got[o3 + 9 * H:o3 + 10 * H], got[o3 + 5 * H:o3 + 6 * H]
+    assert np.any(np.abs(swapped - ref) > bound)
+    dropped = got.copy()
+    dropped[ob3 + 7] -= dY[int(np.argmax(np.abs(dY[:, 7]))), 7]  # the largest of its 256 terms
+    assert np.any(np.abs(dropped - ref) > bound)
+    flipped = got.copy()
+    k = int(np.argmax(np.abs(ref[:H * d])))
+    flipped[k] = -flipped[k]
+    assert np.any(np.abs(flipped - ref) > bound)
