@@ -42,17 +42,23 @@ def parse():
     ap.add_argument("--arith", default="exact", choices=["exact", "f64", "f32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--epochs", type=int, default=200, help="student mode: training epochs")
+    ap.add_argument("--epochs", type=int, default=300, help="student mode: training epochs")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="headline mode: skip the float64 / float32 variants and the peak measurement")
+    ap.add_argument("--no-student", action="store_true", help="headline mode: skip the student fields")
+    ap.add_argument("--student-epochs", type=int, default=60,
+                    help="headline mode: epochs of the student run reported beside the headline")
     ap.add_argument("--workload", default="mlp_d20_l3_b16",
                     choices=["mlp_d20_l3_b16", "uneven_1024", "student", "student_step", "configs",
-                             "value_function"],
+                             "value_function", "peaks"],
                     help="mlp_d20_l3_b16: the headline batch; uneven_1024: 1024 Moebius-sparse "
                          "games with d in 10..20 and l in 1..3, one persistent launch vs "
                          "per-game launches vs a CUDA graph of them; student: the amortised "
                          "explainer; configs: device time of every single-plan configuration "
                          "(each arithmetic, order 4, the other indices), one JSON line; "
                          "value_function: the masked-model value function on each path; "
-                         "student_step: the explainer's training step alone (synthetic batch)")
+                         "student_step: the explainer's training step alone (synthetic batch); "
+                         "peaks: float64 and integer add / multiply-add throughput of this GPU")
     return ap.parse_args()
 
 
@@ -189,6 +195,92 @@ def kernel_traffic(entry=None):
     return t.get("dram_bytes_per_launch")
 
 
+def committed_record(name, entry=None):
+    """A committed ncu figure (profiles/<name>), or None once the kernel's
+    source files differ from the ones profiled."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        if entry is not None:
+            t = t[entry]
+        h = hashlib.sha256()
+        for src in t["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+    except (OSError, ValueError, KeyError):
+        return None
+    if h.hexdigest()[:16] != t.get("sources_sha256_16"):
+        return None
+    return t
+
+
+def measure_alu_peaks(dev, reps=3):
+    """Throughput of float64 add, float64 multiply-add, 32-bit and 64-bit
+    integer add on this GPU (tt_fsi_peak_launch: 8 independent chains per
+    thread, 8 CTAs of 256 threads per SM), best of `reps` launches timed with
+    CUDA events on the launching stream, with the SM clock sampled."""
+    import torch
+    import paper_2601_01903_gb300 as fsi
+    lib = fsi.native.load()
+    props = torch.cuda.get_device_properties(dev)
+    blocks = props.multi_processor_count * 8
+    out = torch.zeros(blocks * 256, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    res = {"sms": props.multi_processor_count, "how": "tt_fsi_peak_launch, 8 independent chains per thread, "
+           f"{blocks} CTAs x 256 threads, best of {reps} launches (CUDA events)"}
+    with ClockSampler(dev.index or 0) as clocks:
+        for kind, name, iters in ((0, "f64_add", 64), (1, "f64_fma", 64), (2, "i32_add", 2048),
+                                  (3, "i64_add", 512)):
+            ops = ctypes.c_int64()
+            best = None
+            for r in range(reps + 1):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st = lib.tt_fsi_peak_launch(kind, blocks, iters, ctypes.c_void_p(out.data_ptr()),
+                                            ctypes.byref(ops), ctypes.c_void_p(stream.cuda_stream))
+                if st != 0:
+                    raise RuntimeError(f"tt_fsi_peak_launch failed ({st})")
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                if r:
+                    ms = e0.elapsed_time(e1)
+                    best = ms if best is None else min(best, ms)
+            res[name + "_per_s"] = ops.value / (best * 1e-3)
+    res["clocks"] = clocks.summary()
+    return res
+
+
+def time_plan(plan, copies, phi, steps, stream, warmup=3, nprof=None):
+    """Device time per step of plan.apply over the rotating input copies
+    (CUDA events on the launching stream), then the tile / combine split of
+    the plan's own tracing over nprof further calls."""
+    import torch
+    import paper_2601_01903_gb300 as fsi
+    for i in range(warmup):
+        plan.apply(copies[i % len(copies)], out=phi)
+    plan.check()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        plan.apply(copies[i % len(copies)], out=phi)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plan.check()
+    lib = fsi.native.load()
+    nprof = nprof or min(steps, 100)
+    lib.tt_fsi_plan_profile(plan.handle, 1)
+    for i in range(nprof):
+        plan.apply(copies[i % len(copies)], out=phi)
+    lib.tt_fsi_plan_profile(plan.handle, 0)
+    t_a, t_b, ncalls = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    lib.tt_fsi_plan_profile_read(plan.handle, ctypes.byref(t_a), ctypes.byref(t_b), ctypes.byref(ncalls))
+    plan.check()
+    n = max(1, ncalls.value)
+    return e0.elapsed_time(e1) / steps, t_a.value / n, t_b.value / n
+
+
 def cpu_baseline(v_host_games, budget_s=12.0):
     """The oracle as it stands, on this host's cores, over whole games of the
     same workload until about budget_s seconds of work."""
@@ -207,6 +299,26 @@ def cpu_baseline(v_host_games, budget_s=12.0):
             "kind": "oracle",
             "sample": f"{done} of the {BATCH} d=20 l=3 masked-MLP games, whole games "
                       f"(closed form, explicit superset sums, OpenMP over scores)"}
+
+
+def cpu_baseline_fast(v_host_games, reps=3):
+    """A fair CPU program on this host's cores (oracle/fsi_cpu_fast.c:
+    Moebius butterflies and weighted pruned superset sums, float64, OpenMP
+    over games) on the whole batch, best of `reps` runs."""
+    import oracle
+    oracle.build()
+    oracle.cpu_fast_fsi(v_host_games[:1], D, ELL)
+    best = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.cpu_fast_fsi(v_host_games, D, ELL)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return {"value": v_host_games.shape[0] * (1 << D) / best, "unit": "coalitions/s",
+            "cores": oracle.num_threads(), "kind": "fast CPU program (not the oracle)",
+            "sample": f"the whole {v_host_games.shape[0]}-game batch, best of {reps} runs "
+                      "(Moebius butterflies + weighted pruned superset sums, blocked for cache, "
+                      "float64, OpenMP over games)"}
 
 
 # ---------------------------------------------------------------------------
@@ -284,9 +396,9 @@ def run_ours(args, rank, world, local_rank):
     ms_per_step = ms / args.steps
     value = whole_job_rate(BATCH * n, world, ms_per_step)
 
-    # per-kernel device time (tracing events on the launching stream): the
-    # fused launch the timed steps ran, and for reference the split schedule
-    # (tile launch, then combine launch)
+    # per-kernel device time (the plan's tracing events on the launching
+    # stream) of the split schedule the timed steps ran (tile launch, then
+    # combine launch), and for comparison the fused persistent schedule
     lib = fsi.native.load()
     nprof = min(args.steps, 100)
 
@@ -323,6 +435,54 @@ def run_ours(args, rank, world, local_rank):
     e2e = {"value": world * BATCH * n / e2e_s, "unit": "coalitions/s",
            "h2d_bytes_per_step": BATCH * n * elem, "d2h_bytes_per_step": BATCH * plan.n_scores * elem}
 
+    # the other arithmetics on the same inputs: float64 throughout (the
+    # literal reading of the exact path, bound by the float64 pipe) and
+    # float32 (with its measured error against the exact path, whose own
+    # parity with the oracle the tests establish)
+    variants, alu = None, None
+    if not args.no_variants and args.arith == "exact":
+        alu = measure_alu_peaks(dev)
+        ref = phi.double().clone()
+        vmax = v.abs().amax(dim=1)
+        variants = {}
+        for arith in ("f64", "f32"):
+            vp = fsi.Plan(D, ELL, arith, max_batch=BATCH)
+            cps = [c.float() for c in copies] if arith == "f32" else copies
+            out = torch.empty((BATCH, vp.n_scores), dtype=cps[0].dtype, device=dev)
+            steps = max(5, min(args.steps, 50))
+            with ClockSampler(local_rank) as vclocks:
+                ms_v, t_tile, t_comb = time_plan(vp, cps, out, steps, stream)
+            vp.apply(copies[0].float() if arith == "f32" else copies[0], out=out)
+            torch.cuda.synchronize()
+            err = ((out.double() - ref).abs().amax(dim=1) / vmax).max().item()
+            el = 4 if arith == "f32" else 8
+            ach = BATCH * n * el / (t_tile * 1e-3) / 1e9
+            entry = {"value": whole_job_rate(BATCH * n, world, ms_v), "unit": "coalitions/s",
+                     "ms_per_step": ms_v, "dtype": arith, "steps": steps,
+                     "tile_kernel_ms": t_tile, "combine_kernel_ms": t_comb,
+                     "max_err_vs_exact_rel_maxv": err,
+                     "roofline_hbm": {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                      "peak_kind": peak_kind},
+                     "clocks": vclocks.summary()}
+            if arith == "f64":
+                rec = committed_record("fp64_ops.json")
+                if rec is not None:
+                    ops = float(rec["fp64_thread_inst_per_launch"])
+                    pk = max(alu["f64_add_per_s"], alu["f64_fma_per_s"])
+                    entry["roofline_fp64"] = {
+                        "bound": "fp64_alu", "kernel": rec["kernel"], "achieved": ops / (t_tile * 1e-3),
+                        "peak": pk, "unit": "float64 instructions/s", "frac": ops / (t_tile * 1e-3) / pk,
+                        "peak_kind": "measured live (tt_fsi_peak_launch, best of add and multiply-add)",
+                        "fp64_thread_inst_per_launch": ops, "ops_source": "profiles/fp64_ops.json (ncu)"}
+                else:
+                    entry["roofline_fp64"] = None
+            variants[arith] = entry
+            vp.close()
+
+    student = None
+    if not args.no_student and world == 1:
+        student = student_run(dev, args.student_epochs, full=False)
+
     if rank != 0:
         return
     line = {
@@ -345,8 +505,15 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e,
         "gpu_launches": 2 * args.steps,
     }
+    if variants is not None:
+        line["variants"] = variants
+        line["alu_peaks"] = alu
+    if student is not None:
+        line["student"] = student
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(copies[0][:4].cpu().numpy())
+        vh = copies[0].cpu().numpy() if args.arith != "f32" else copies[0].double().cpu().numpy()
+        line["cpu_baseline"] = cpu_baseline(vh[:4])
+        line["cpu_baseline_fast"] = cpu_baseline_fast(vh)
     print(json.dumps(line), flush=True)
 
 
@@ -379,6 +546,12 @@ def run_configs(args, rank, world, local_rank):
                 gens[name] = masked(synthetic.workload_mlp_d20())
             elif name == "d24":
                 gens[name] = masked(synthetic.workload_mlp_d24())
+            elif name == "n20":
+                # white noise at the headline size: the float32 arithmetic's
+                # worst case (cancellation in the alternating-sign sums)
+                g = torch.Generator(device=dev)
+                g.manual_seed(20)
+                gens[name] = torch.randn((16, 1 << 20), dtype=torch.float64, device=dev, generator=g)
             elif name == "d28":
                 # device time does not depend on the values: seeded noise,
                 # one game of 2^28 coalitions (2 GiB)
@@ -388,11 +561,13 @@ def run_configs(args, rank, world, local_rank):
         return gens[name]
 
     rows = []
+    exact_out = {}
     specs = [("cfg1 Moebius game d=8 l=2 B=1", "d8", 8, 2),
              ("cfg2 masked MLP d=14 l=2 B=64", "d14", 14, 2),
              ("cfg3a masked MLP d=20 l=3 B=16", "d20", 20, 3),
              ("cfg3b masked MLP d=24 l=2 B=1", "d24", 24, 2),
              ("order 4, masked MLP d=20 B=16", "d20", 20, 4),
+             ("white noise d=20 l=3 B=16", "n20", 20, 3),
              ("large d: noise game d=28 l=3 B=1", "d28", 28, 3)]
     for label, key, d, ell in specs:
         v64 = inputs(key)
@@ -418,10 +593,22 @@ def run_configs(args, rank, world, local_rank):
                 plan.check()
                 ms = e0.elapsed_time(e1) / reps
                 elem = 4 if arith == "f32" else 8
-                rows.append({"config": label, "index": index, "arith": arith, "d": d, "ell": ell, "B": B,
-                             "ms_per_call": ms, "coalitions_per_s": B * (1 << d) / (ms * 1e-3),
-                             "hbm_frac_of_measured": B * (1 << d) * elem / (ms * 1e-3) / 1e9 / peaks()[0],
-                             "calls_timed": reps, "variant": "default"})
+                row = {"config": label, "index": index, "arith": arith, "d": d, "ell": ell, "B": B,
+                       "ms_per_call": ms, "coalitions_per_s": B * (1 << d) / (ms * 1e-3),
+                       "hbm_frac_of_measured": B * (1 << d) * elem / (ms * 1e-3) / 1e9 / peaks()[0],
+                       "calls_timed": reps, "variant": "default"}
+                # error against the exact arithmetic on the same input (the
+                # exact path's own parity with the oracle is a test), per
+                # game as max |difference| / max |v|, the worst game reported
+                plan.apply(v, out=out)
+                torch.cuda.synchronize()
+                if arith == "exact":
+                    exact_out[(key, ell, index)] = out.clone()
+                else:
+                    ref = exact_out[(key, ell, index)]
+                    vmax = v64.abs().amax(dim=1)
+                    row["max_err_vs_exact_rel_maxv"] = ((out.double() - ref).abs().amax(dim=1) / vmax).max().item()
+                rows.append(row)
                 plan.close()
     # the comparison variants: the same scores by the site-by-site sweep, and
     # by the sweep of the precontracted operator on v
@@ -605,20 +792,19 @@ def run_uneven(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
-def run_student(args, rank, world, local_rank):
+def student_run(dev, epochs, full=True):
     """Amortised explainer: d=16, l=2 (137 scores), teacher 16-128-128-1,
     x ~ N(0, Sigma) with Sigma_ij = 0.5^|i-j|; 200k training / 10k held-out
-    pairs labelled by the exact path; student 16-1024-1024-137, batch 4096.
-    Reports training throughput (GEMM TFLOP/s), inference instances/s with
-    and without the residual check, the exact path's instances/s, and the
-    student's error against exact FSI on the held-out set."""
+    pairs labelled by the exact path; student 16-1024-1024-137, batch 4096,
+    cosine learning-rate decay.  Returns training throughput (GEMM
+    TFLOP/s), inference instances/s with and without the residual check,
+    the exact path's instances/s, and the student's error against exact FSI
+    on the held-out set."""
     import numpy as np
     import torch
     from paper_2601_01903_gb300 import student as st, synthetic
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
     H, BATCH_S, N_TRAIN, N_HELD = 1024, 4096, 200_000, 10_000
-    epochs = max(1, args.epochs)
+    epochs = max(1, epochs)
     ex = st.Explainer(synthetic.workload_student_teacher(), ell=2, hidden=H, batch=BATCH_S)
     t0 = time.perf_counter()
     train = ex.dataset(N_TRAIN, first=0)
@@ -629,9 +815,9 @@ def run_student(args, rank, world, local_rank):
     nb = N_TRAIN // BATCH_S
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream(dev)
-    with ClockSampler(local_rank) as clocks:
+    with ClockSampler(dev.index or 0) as clocks:
         e0.record(stream)
-        losses = ex.train(train, epochs=epochs, lr=1e-3)
+        losses = ex.train(train, epochs=epochs, lr=2e-3, schedule="cosine")
         e1.record(stream)
         torch.cuda.synchronize()
     ms_train = e0.elapsed_time(e1)
@@ -651,6 +837,12 @@ def run_student(args, rank, world, local_rank):
     rel = (torch.linalg.norm(phi - lab) / torch.linalg.norm(lab)).item()
     out, fb = ex.explain(held.x, held.target, first=N_TRAIN)
     rel_fb = (torch.linalg.norm(out - lab) / torch.linalg.norm(lab)).item()
+    # baselines the student must beat: the training mean, and least squares on [x, 1]
+    mean_rel = (torch.linalg.norm(train.labels.double().mean(0) - lab) / torch.linalg.norm(lab)).item()
+    Xtr = torch.cat([train.x.double(), torch.ones(train.x.shape[0], 1, device=dev, dtype=torch.float64)], 1)
+    Xh = torch.cat([held.x.double(), torch.ones(held.x.shape[0], 1, device=dev, dtype=torch.float64)], 1)
+    coef = torch.linalg.lstsq(Xtr, train.labels.double()).solution
+    lin_rel = (torch.linalg.norm(Xh @ coef - lab) / torch.linalg.norm(lab)).item()
 
     def rate(fn, n, reps=5):
         fn()
@@ -668,31 +860,60 @@ def run_student(args, rank, world, local_rank):
     ips_checked = rate(lambda: ex.explain(xb, tb, first=N_TRAIN), BATCH_S)
     x64 = held.x[:1024].double()
     ips_exact = rate(lambda: ex.exact(x64), 1024, reps=2)
-    ips_exact_f32 = rate(lambda: ex.exact(x64, tc=False), 1024, reps=2)
+    res = {
+        "student_inst_per_s": ips_checked, "student_only_inst_per_s": ips_student,
+        "exact_path_inst_per_s": ips_exact, "speedup_vs_exact": ips_checked / ips_exact,
+        "heldout_rel_error": rel, "heldout_rel_error_after_fallback": rel_fb, "heldout_rmse": rmse,
+        "baseline_rel_error_mean": mean_rel, "baseline_rel_error_linear": lin_rel,
+        "fallback_fraction": fb.float().mean().item(), "epochs": epochs, "train_step_ms": ms_train / steps,
+        "train_tflops": tflops, "final_train_loss": losses[-1], "data_generation_s": t_data,
+        "threshold": tau, "label_rel_diff_tc_vs_fp32_values": label_rel_diff,
+        "config": {"workload": "student_d16_l2", "hidden": H, "batch": BATCH_S, "train": N_TRAIN,
+                   "held_out": N_HELD, "residual_samples": ex.K, "lr": "2e-3 cosine to 0"},
+        "clocks": clocks.summary(),
+    }
+    if full:
+        res["exact_path_fp32_values_inst_per_s"] = rate(lambda: ex.exact(x64, tc=False), 1024, reps=2)
+        res["value_path"] = "tcgen05 BF16 layer 2" if ex.tc else "FP32 CUDA cores"
+        res["steps"] = steps
+    return res
+
+
+def run_student(args, rank, world, local_rank):
+    """The amortised explainer on its own line (see student_run)."""
+    import torch
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    r = student_run(dev, args.epochs, full=True)
     mb = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops_sustained": 1700.0}
     if rank != 0:
         return
+    pk = float(mb.get("bf16_tflops_sustained", 1700.0))
     line = {
-        "metric": "student inst/s (amortised explainer, d=16 l=2, 137 scores)", "value": ips_checked,
-        "unit": "instances/s", "n_gpus": world, "steps": epochs, "warmup": 0, "ms_per_step": ms_train / steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": "student_d16_l2", "hidden": H, "batch": BATCH_S, "train": N_TRAIN, "held_out": N_HELD,
-                   "epochs": epochs, "residual_samples": ex.K, "threshold": tau},
-        "student_only_inst_per_s": ips_student, "exact_path_inst_per_s": ips_exact,
-        "exact_path_fp32_values_inst_per_s": ips_exact_f32, "speedup_vs_exact": ips_checked / ips_exact,
-        "value_path": "tcgen05 BF16 layer 2" if ex.tc else "FP32 CUDA cores",
-        "label_rel_diff_tc_vs_fp32_values": label_rel_diff,
-        "heldout_rmse": rmse, "heldout_rel_error": rel, "heldout_rel_error_after_fallback": rel_fb,
-        "fallback_fraction": fb.float().mean().item(), "final_train_loss": losses[-1],
-        "data_generation_s": t_data,
-        "roofline": {"bound": "tensor", "kernel": "gemm_bf16_tcgen05 (training step)", "achieved": tflops,
-                     "peak": float(mb.get("bf16_tflops_sustained", 1700.0)), "unit": "TFLOP/s",
-                     "frac": tflops / float(mb.get("bf16_tflops_sustained", 1700.0)), "traffic": None},
-        "clocks": clocks.summary(),
-        "gpu_launches": steps * 16,
+        "metric": "student inst/s (amortised explainer, d=16 l=2, 137 scores)", "value": r["student_inst_per_s"],
+        "unit": "instances/s", "n_gpus": world, "steps": r["epochs"], "warmup": 0,
+        "ms_per_step": r["train_step_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16", "data": "synthetic", "config": r["config"],
+        "roofline": {"bound": "tensor", "kernel": "gemm_bf16_tcgen05 (training step)", "achieved": r["train_tflops"],
+                     "peak": pk, "unit": "TFLOP/s", "frac": r["train_tflops"] / pk, "traffic": None},
+        "clocks": r["clocks"], "gpu_launches": r["steps"] * 16,
     }
+    line.update({k: v for k, v in r.items() if k not in ("config", "clocks")})
     print(json.dumps(line), flush=True)
+
+
+def run_peaks(args, rank, world, local_rank):
+    """Arithmetic throughput of this GPU: float64 add and multiply-add, 32-
+    and 64-bit integer add (the ALU rooflines of the float64 and the exact
+    arithmetic)."""
+    import torch
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    r = measure_alu_peaks(dev, reps=max(3, args.steps if args.steps < 50 else 5))
+    if rank == 0:
+        print(json.dumps({"metric": "arithmetic throughput per GPU", "unit": "operations/s", "n_gpus": 1,
+                          "data": "synthetic", **r}), flush=True)
 
 
 def main():
@@ -719,6 +940,8 @@ def main():
             run_value_function(args, rank, world, local_rank)
         elif args.workload == "student_step":
             run_student_step(args, rank, world, local_rank)
+        elif args.workload == "peaks":
+            run_peaks(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

@@ -32,6 +32,8 @@ What is here:
   scores (pure Python over the score list).
 * ``masked_game`` -- the model value function with absent features set to a
   baseline, one forward pass per coalition (C).
+* ``cpu_fast_fsi`` -- not the oracle: the timed fast CPU baseline
+  (``fsi_cpu_fast.c``), checked against ``fsi`` by the tests.
 * ``mpo_sweep`` -- the paper's own route (Section 3.3 MPO with Algorithm 1's
   left-to-right sweep), pure Python over explicit states; used only to check
   the paper's structural claims (state counts, transitions) and that the
@@ -58,23 +60,53 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fsi_oracle.c")
+_FAST_SRC = os.path.join(_HERE, "fsi_cpu_fast.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_FAST_PATH = os.path.join(_BUILD, "libcpufast.so")
 _lock = threading.Lock()
 _lib = None
+_fast = None
+
+
+def _compile(src: str, out: str, flags, force: bool):
+    stale = (not os.path.exists(out)) or os.path.getmtime(out) < os.path.getmtime(src)
+    if force or stale:
+        tmp = out + f".{os.getpid()}.tmp"
+        subprocess.run(["gcc"] + list(flags) + ["-fPIC", "-shared", "-std=c11", "-o", tmp, src, "-lm"],
+                       check=True)
+        os.replace(tmp, out)
 
 
 def build(force: bool = False) -> str:
-    """Compile the C core with gcc (OpenMP, no fused multiply-add)."""
+    """Compile the C core with gcc (OpenMP, no fused multiply-add), and the
+    fast CPU baseline (fsi_cpu_fast.c, -O3, OpenMP)."""
     os.makedirs(_BUILD, exist_ok=True)
-    stale = (not os.path.exists(_LIB_PATH)) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)
-    if force or stale:
-        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11",
-               "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
+    _compile(_SRC, _LIB_PATH, ["-O2", "-fopenmp", "-ffp-contract=off"], force)
+    _compile(_FAST_SRC, _FAST_PATH, ["-O3", "-fopenmp"], force)
     return _LIB_PATH
+
+
+def cpu_fast_fsi(v, d: int, ell: int) -> np.ndarray:
+    """FSI scores [B, n_scores] by the fast CPU program of fsi_cpu_fast.c
+    (Moebius butterflies, weighted pruned superset sums; float64, OpenMP over
+    games) -- the timed CPU baseline, not the oracle; the tests check it
+    against ``fsi``."""
+    global _fast
+    with _lock:
+        if _fast is None:
+            build()
+            lib = ctypes.CDLL(_FAST_PATH)
+            lib.cpu_fast_fsi.restype = ctypes.c_int
+            lib.cpu_fast_fsi.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                         ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+            _fast = lib
+    v = _as_games(v, d)
+    m = score_masks(d, ell)
+    out = np.empty((v.shape[0], m.shape[0]), dtype=np.float64)
+    if _fast.cpu_fast_fsi(d, ell, v.shape[0], _ptr(v), m.shape[0], _ptr(m), _ptr(out)) != 0:
+        raise RuntimeError("cpu_fast_fsi failed")
+    return out
 
 
 def _load():

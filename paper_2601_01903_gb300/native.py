@@ -170,6 +170,8 @@ def _declare(lib):
     lib.tt_fsi_batch_set_wait_limit.argtypes = [vp, c.c_longlong, i]
     lib.tt_fsi_batch_check.restype = i
     lib.tt_fsi_batch_check.argtypes = [vp, vp]
+    lib.tt_fsi_peak_launch.restype = i
+    lib.tt_fsi_peak_launch.argtypes = [i, i, i, vp, c.POINTER(i64), vp]
     lib.tt_fsi_gemm_bf16.restype = i
     lib.tt_fsi_gemm_bf16.argtypes = [vp, i, vp, i, i, i, i, vp, i, vp, i, vp, i, vp, i, vp, i, vp, vp]
     for name, args, res in EXTRA_SIGNATURES:

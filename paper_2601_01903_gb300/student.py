@@ -275,7 +275,11 @@ class Explainer:
         return Dataset(x64.float(), labels, self.targets(x64), self.v_empty)
 
     # -- training -------------------------------------------------------------
-    def train(self, data: Dataset, epochs: int, lr: float = 1e-3, seed: int = 4, log=None):
+    def train(self, data: Dataset, epochs: int, lr: float = 1e-3, seed: int = 4, log=None,
+              schedule: str = "constant"):
+        """Adam over the fixed batches of ``data`` for ``epochs`` epochs;
+        schedule "cosine" decays the learning rate from lr towards 0 over
+        the run (one value per epoch), "constant" keeps it."""
         torch = self.torch
         self.student.set_adam(lr=lr)
         n = data.x.shape[0]
@@ -285,6 +289,8 @@ class Explainer:
         # The instances are i.i.d. draws, so each epoch visits the fixed
         # batches in a fresh random order (no per-step gathers).
         for ep in range(epochs):
+            if schedule == "cosine":
+                self.student.set_adam(lr=lr * 0.5 * (1.0 + math.cos(math.pi * ep / epochs)))
             order = np.argsort(perm_stream.uniform(nb))
             for b in order:
                 sl = slice(int(b) * self.batch, (int(b) + 1) * self.batch)

@@ -395,3 +395,17 @@ def test_direct_route_equals_closed_form(oracle_mod, d, ell):
     masks = [int(m) for m in oracle_mod.score_masks(d, ell)]
     got = oracle_mod.fsi_direct(v, d, ell, masks)
     assert np.max(np.abs(got - oracle_mod.fsi(v, d, ell)[0])) <= 1e-13 * np.max(np.abs(v))
+
+
+# --------------------------------------------------------------------------
+# the fast CPU baseline (timed beside the GPU) agrees with the oracle
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d,ell,B", [(1, 1, 1), (3, 2, 2), (8, 2, 3), (12, 3, 2), (15, 3, 1), (16, 2, 2),
+                                     (14, 4, 1), (9, 9, 1), (10, 12, 1)])
+def test_cpu_fast_baseline_matches_oracle(oracle_mod, d, ell, B):
+    v = np.random.default_rng(d * 100 + ell).normal(size=(B, 1 << d))
+    got = oracle_mod.cpu_fast_fsi(v, d, ell)
+    ref = oracle_mod.fsi(v, d, ell)
+    assert got.shape == ref.shape
+    assert np.max(np.abs(got - ref)) <= 1e-10 * np.abs(v).max()
