@@ -46,8 +46,11 @@ def parse():
     ap.add_argument("--no-variants", action="store_true",
                     help="headline mode: skip the float64 / float32 variants and the peak measurement")
     ap.add_argument("--no-student", action="store_true", help="headline mode: skip the student fields")
-    ap.add_argument("--student-epochs", type=int, default=60,
+    ap.add_argument("--student-epochs", type=int, default=300,
                     help="headline mode: epochs of the student run reported beside the headline")
+    ap.add_argument("--student-lr", type=float, default=2e-3, help="student: peak learning rate")
+    ap.add_argument("--student-schedule", default="cosine", choices=["cosine", "constant"],
+                    help="student: learning-rate schedule")
     ap.add_argument("--workload", default="mlp_d20_l3_b16",
                     choices=["mlp_d20_l3_b16", "uneven_1024", "student", "student_step", "configs",
                              "value_function", "peaks"],
@@ -467,13 +470,20 @@ def run_ours(args, rank, world, local_rank):
             if arith == "f64":
                 rec = committed_record("fp64_ops.json")
                 if rec is not None:
-                    ops = float(rec["fp64_thread_inst_per_launch"])
-                    pk = max(alu["f64_add_per_s"], alu["f64_fma_per_s"])
+                    # the float64 pipe's time for this launch's instruction mix
+                    # at the measured rates, over the measured kernel time
+                    n_add = float(rec["dadd_thread_inst_per_launch"] + rec["dmul_thread_inst_per_launch"])
+                    n_fma = float(rec["dfma_thread_inst_per_launch"])
+                    ops = n_add + n_fma
+                    pk = ops / (n_add / alu["f64_add_per_s"] + n_fma / alu["f64_fma_per_s"])
                     entry["roofline_fp64"] = {
                         "bound": "fp64_alu", "kernel": rec["kernel"], "achieved": ops / (t_tile * 1e-3),
                         "peak": pk, "unit": "float64 instructions/s", "frac": ops / (t_tile * 1e-3) / pk,
-                        "peak_kind": "measured live (tt_fsi_peak_launch, best of add and multiply-add)",
-                        "fp64_thread_inst_per_launch": ops, "ops_source": "profiles/fp64_ops.json (ncu)"}
+                        "peak_kind": "measured live (tt_fsi_peak_launch: add and multiply-add rates, "
+                                     "weighted by the kernel's instruction mix)",
+                        "fp64_thread_inst_per_launch": ops,
+                        "fp64_inst_per_coalition": ops / (BATCH * n),
+                        "ops_source": "profiles/fp64_ops.json (ncu, same sources)"}
                 else:
                     entry["roofline_fp64"] = None
             variants[arith] = entry
@@ -481,7 +491,8 @@ def run_ours(args, rank, world, local_rank):
 
     student = None
     if not args.no_student and world == 1:
-        student = student_run(dev, args.student_epochs, full=False)
+        student = student_run(dev, args.student_epochs, full=False, lr=args.student_lr,
+                              schedule=args.student_schedule)
 
     if rank != 0:
         return
@@ -792,7 +803,7 @@ def run_uneven(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
-def student_run(dev, epochs, full=True):
+def student_run(dev, epochs, full=True, lr=2e-3, schedule="cosine"):
     """Amortised explainer: d=16, l=2 (137 scores), teacher 16-128-128-1,
     x ~ N(0, Sigma) with Sigma_ij = 0.5^|i-j|; 200k training / 10k held-out
     pairs labelled by the exact path; student 16-1024-1024-137, batch 4096,
@@ -817,7 +828,7 @@ def student_run(dev, epochs, full=True):
     stream = torch.cuda.current_stream(dev)
     with ClockSampler(dev.index or 0) as clocks:
         e0.record(stream)
-        losses = ex.train(train, epochs=epochs, lr=2e-3, schedule="cosine")
+        losses = ex.train(train, epochs=epochs, lr=lr, schedule=schedule)
         e1.record(stream)
         torch.cuda.synchronize()
     ms_train = e0.elapsed_time(e1)
@@ -869,7 +880,7 @@ def student_run(dev, epochs, full=True):
         "train_tflops": tflops, "final_train_loss": losses[-1], "data_generation_s": t_data,
         "threshold": tau, "label_rel_diff_tc_vs_fp32_values": label_rel_diff,
         "config": {"workload": "student_d16_l2", "hidden": H, "batch": BATCH_S, "train": N_TRAIN,
-                   "held_out": N_HELD, "residual_samples": ex.K, "lr": "2e-3 cosine to 0"},
+                   "held_out": N_HELD, "residual_samples": ex.K, "lr": lr, "schedule": schedule},
         "clocks": clocks.summary(),
     }
     if full:
@@ -884,7 +895,7 @@ def run_student(args, rank, world, local_rank):
     import torch
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    r = student_run(dev, args.epochs, full=True)
+    r = student_run(dev, args.epochs, full=True, lr=args.student_lr, schedule=args.student_schedule)
     mb = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops_sustained": 1700.0}
     if rank != 0:

@@ -118,31 +118,47 @@ def loss_and_grads(params, x, labels, target, v_empty, d, H, n_out, emulate_bf16
     return loss, grads
 
 
+def _forward_scales(params, x, d, H, n_out):
+    """Root-sum-square scales of the forward pass with BF16 rounding points
+    kept: s(Z1) = sqrt(X^2 (W1^2)^T + b1^2), s(A1) = |A1| + |gelu'(Z1)| s(Z1),
+    and so on through layer 2 and the output.  Changing any one rounded
+    operand upstream by a relative 2^-8 moves each entry by at most about
+    2^-8 times its scale."""
+    f = forward(params, x, d, H, n_out, emulate_bf16=True)
+    P = unpack(params, d, H, n_out)
+    sZ1 = np.sqrt(f["X"] ** 2 @ (f["W1"] ** 2).T + P["b1"] ** 2)
+    sA1 = np.abs(f["A1"]) + np.abs(gelu_grad(f["Z1"])) * sZ1
+    sZ2 = np.sqrt(sA1 ** 2 @ (f["W2"] ** 2).T + P["b2"] ** 2)
+    sA2 = np.abs(f["A2"]) + np.abs(gelu_grad(f["Z2"])) * sZ2
+    sY = np.sqrt(sA2 ** 2 @ (f["W3"] ** 2).T + P["b3"] ** 2)
+    return f, sA1, sA2, sY
+
+
 def grad_magnitudes(params, x, labels, target, v_empty, d, H, n_out):
     """Per-entry scale for comparing GPU gradients with ``loss_and_grads``:
     the same backward pass with every sum replaced by the root of the sum of
-    its squared terms (BF16 rounding points kept), each intermediate carried
-    as that root-sum-square scale.  Changing one rounded operand by a
-    relative 2^-8 (one BF16 ulp) changes one term of each sum it feeds, so it
-    moves gradient k by at most 2^-8 times this scale; FP32 accumulation in
+    its squared terms (BF16 rounding points kept), each forward operand by
+    its scale from ``_forward_scales`` and each intermediate carried as that
+    root-sum-square scale.  Changing one rounded operand by a relative 2^-8
+    (one BF16 ulp) changes one term of each sum it feeds, so it moves
+    gradient k by at most about 2^-8 times this scale; FP32 accumulation in
     another order moves it by far less.  Element-wise tolerances are
     multiples of 2^-8 times this value."""
-    f = forward(params, x, d, H, n_out, emulate_bf16=True)
+    f, sA1, sA2, sY = _forward_scales(params, x, d, H, n_out)
     B = f["Y"].shape[0]
     phi = project(f["Y"], target, v_empty)
-    rY = np.sqrt(f["A2"] ** 2 @ f["W3"].T ** 2 + unpack(params, d, H, n_out)["b3"] ** 2)
     # |d loss / d Y| and the scale of its changes: the error, plus the
-    # output scale (a flip in the forward pass moves Y by 2^-8 of it)
-    e = np.abs(phi - labels) + rY
+    # output scale (an upstream flip moves Y by 2^-8 of it)
+    e = np.abs(phi - labels) + sY
     g = 2.0 * e / (B * n_out)
     dY = np.zeros_like(g)
     dY[:, 1:] = np.sqrt(g[:, 1:] ** 2 + (g[:, 1:] ** 2).mean(axis=1, keepdims=True))
     sq = lambda a: np.asarray(a, dtype=np.float64) ** 2
     gp2, gp1 = np.abs(gelu_grad(f["Z2"])), np.abs(gelu_grad(f["Z1"]))
-    mW3 = np.sqrt(sq(dY).T @ sq(f["A2"]))
+    mW3 = np.sqrt(sq(dY).T @ sq(sA2))
     mb3 = np.sqrt(sq(dY).sum(axis=0))
     dH2 = np.sqrt(sq(dY) @ sq(f["W3"])) * gp2
-    mW2 = np.sqrt(sq(dH2).T @ sq(f["A1"]))
+    mW2 = np.sqrt(sq(dH2).T @ sq(sA1))
     mb2 = np.sqrt(sq(dH2).sum(axis=0))
     dH1 = np.sqrt(sq(dH2) @ sq(f["W2"])) * gp1
     mW1 = np.sqrt(sq(dH1).T @ sq(f["X"]))
@@ -151,12 +167,10 @@ def grad_magnitudes(params, x, labels, target, v_empty, d, H, n_out):
 
 
 def output_magnitudes(params, x, d, H, n_out):
-    """Per-entry root-sum-square scale of the raw outputs,
-    sqrt(A2^2 (W3^2)^T + b3^2) (BF16 rounding points kept), the scale of
-    element-wise tolerances on forward passes (see grad_magnitudes)."""
-    f = forward(params, x, d, H, n_out, emulate_bf16=True)
-    P = unpack(params, d, H, n_out)
-    return np.sqrt(f["A2"] ** 2 @ (f["W3"] ** 2).T + P["b3"] ** 2)
+    """Per-entry scale of the raw outputs (``_forward_scales``): the bound on
+    how far BF16 rounding flips anywhere in the forward pass can move them,
+    in units of 2^-8."""
+    return _forward_scales(params, x, d, H, n_out)[3]
 
 
 def adam_step(p, m, v, g, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):

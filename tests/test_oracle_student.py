@@ -119,3 +119,23 @@ def test_gradient_scale_separates_rounding_from_mistakes():
     k = int(np.argmax(np.abs(ref[:H * d])))
     flipped[k] = -flipped[k]
     assert np.any(np.abs(flipped - ref) > bound)
+
+
+def test_output_scale_bounds_an_upstream_bf16_flip():
+    """Moving one layer-1 activation by one BF16 ulp changes every output of
+    its instance; the change stays within 2^-8 times the forward scale."""
+    from paper_2601_01903_gb300 import student as st
+    d, H, n_out, B = 16, 64, 137, 64
+    params = st.init_params(d, H, n_out, 2).astype(np.float64)
+    x = np.random.default_rng(2).normal(size=(B, d)).astype(np.float32)
+    f = so.forward(params, x, d, H, n_out, emulate_bf16=True)
+    mag = so.output_magnitudes(params, x, d, H, n_out)
+    P = so.unpack(params, d, H, n_out)
+    worst = 0.0
+    for b, i in ((0, 0), (5, 17), (40, 63)):
+        A1 = f["A1"].copy()
+        A1[b, i] *= 1 + 2.0 ** -8
+        A2 = so.bf16_round(so.gelu(A1 @ f["W2"].T + P["b2"]))
+        Y = A2 @ f["W3"].T + P["b3"]
+        worst = max(worst, float(np.max(np.abs(Y - f["Y"]) / mag)))
+    assert 0 < worst <= 4 * 2.0 ** -8
