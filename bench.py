@@ -42,13 +42,13 @@ def parse():
     ap.add_argument("--arith", default="exact", choices=["exact", "f64", "f32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--epochs", type=int, default=300, help="student mode: training epochs")
+    ap.add_argument("--epochs", type=int, default=1000, help="student mode: training epochs")
     ap.add_argument("--no-variants", action="store_true",
                     help="headline mode: skip the float64 / float32 variants and the peak measurement")
     ap.add_argument("--no-student", action="store_true", help="headline mode: skip the student fields")
-    ap.add_argument("--student-epochs", type=int, default=300,
+    ap.add_argument("--student-epochs", type=int, default=1000,
                     help="headline mode: epochs of the student run reported beside the headline")
-    ap.add_argument("--student-lr", type=float, default=2e-3, help="student: peak learning rate")
+    ap.add_argument("--student-lr", type=float, default=1e-3, help="student: peak learning rate")
     ap.add_argument("--student-schedule", default="cosine", choices=["cosine", "constant"],
                     help="student: learning-rate schedule")
     ap.add_argument("--workload", default="mlp_d20_l3_b16",
@@ -803,7 +803,7 @@ def run_uneven(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
-def student_run(dev, epochs, full=True, lr=2e-3, schedule="cosine"):
+def student_run(dev, epochs, full=True, lr=1e-3, schedule="cosine"):
     """Amortised explainer: d=16, l=2 (137 scores), teacher 16-128-128-1,
     x ~ N(0, Sigma) with Sigma_ij = 0.5^|i-j|; 200k training / 10k held-out
     pairs labelled by the exact path; student 16-1024-1024-137, batch 4096,

@@ -88,10 +88,10 @@ def test_adam_step_and_projection_match_oracle():
     ref = so.project(f["Y"], target, v0)
     # element-wise: the projection shifts every non-empty score by the mean
     # residual, so its scale is the raw outputs' plus their mean
+    # (score 0 is v(empty) in float32, checked above)
     mag = so.output_magnitudes(p1.astype(np.float64), x, d, H, n_out)
     mag[:, 1:] += mag[:, 1:].mean(axis=1, keepdims=True)
-    mag[:, 0] = 0.0
-    _elementwise(phi, ref, mag + 1e-6 * np.abs(target)[:, None], "projected outputs")
+    _elementwise(phi[:, 1:], ref[:, 1:], mag[:, 1:] + 1e-6 * np.abs(target)[:, None], "projected outputs")
 
 
 def test_checkpoint_resume_is_bitwise(tmp_path):
