@@ -35,9 +35,17 @@ TTFSI_HD constexpr int rank4(int x) { return (int)((0x0325143302120100ull >> (4 
 
 // level-4 states of round rd: (sigma_A, t), t in [rd, 4]
 TTFSI_HD constexpr int n4(int rd) { return c4(rd) * (5 - rd); }
-TTFSI_HD constexpr int n4_max(int L) {
+
+// A round's states can be processed in chunks of consecutive ranks of
+// sigma_A, so that only one chunk's level-4 and level-8 states are held in
+// shared memory at a time: with CH (chunked) the rounds with 4 or 6
+// patterns sigma_A (rd = 1, 2) in two chunks, the others whole; without,
+// every round whole.
+TTFSI_HD constexpr int n_chunks(int rd, bool CH) { return CH && (rd == 1 || rd == 2) ? 2 : 1; }
+TTFSI_HD constexpr int chunk_a(int rd, bool CH) { return c4(rd) / n_chunks(rd, CH); }
+TTFSI_HD constexpr int n4c_max(int L, bool CH) {
     int m = 0;
-    for (int rd = 0; rd <= L; ++rd) m = n4(rd) > m ? n4(rd) : m;
+    for (int rd = 0; rd <= L; ++rd) m = chunk_a(rd, CH) * (5 - rd) > m ? chunk_a(rd, CH) * (5 - rd) : m;
     return m;
 }
 
@@ -48,13 +56,12 @@ TTFSI_HD constexpr int off8(int rd, int kB) {
            (kB > 3 ? 4 * (6 - rd) : 0) + (kB > 4 ? (5 - rd) : 0);
 }
 TTFSI_HD constexpr int s8(int L, int rd) { return off8(rd, L - rd + 1); }
-TTFSI_HD constexpr int n8(int L, int rd) { return c4(rd) * s8(L, rd); }
-// Row stride of the level-8 region [tau_C][state]: the largest round, made
+// Row stride of the level-8 region [tau_C][state]: the largest chunk, made
 // odd so that both the writes (16 tau_C, one state) and the reads (one
 // tau_C, consecutive states) fall on distinct 8-byte bank pairs.
-TTFSI_HD constexpr int nst(int L) {
+TTFSI_HD constexpr int nst(int L, bool CH) {
     int m = 0;
-    for (int rd = 0; rd <= L; ++rd) m = n8(L, rd) > m ? n8(L, rd) : m;
+    for (int rd = 0; rd <= L; ++rd) m = chunk_a(rd, CH) * s8(L, rd) > m ? chunk_a(rd, CH) * s8(L, rd) : m;
     return m | 1;
 }
 
@@ -75,14 +82,19 @@ TTFSI_HD constexpr int chan_group(int L, int rd, int kB) {
 }
 TTFSI_HD constexpr int n_chan(int L) { return chan_group(L, L + 1, 0); }
 
-// block-3 items of round rd and group kB: (rank sigma_A, rank sigma_B, u'),
-// u' in [rd + kB, 12]; each group padded to whole warps
-TTFSI_HD constexpr int g3(int rd, int kB) { return c4(rd) * c4(kB) * (13 - rd - kB); }
+// block-3 items of one chunk of round rd and group kB: (rank sigma_A,
+// rank sigma_B, u'), u' in [rd + kB, 12]; each group padded to whole warps
+TTFSI_HD constexpr int g3(int rd, int kB, bool CH) { return chunk_a(rd, CH) * c4(kB) * (13 - rd - kB); }
 TTFSI_HD constexpr int pad32(int n) { return (n + 31) & ~31; }
 
-// shared-memory regions in elements
-TTFSI_HD constexpr int regA_elems(int L) { return 16 * nst(L) > 4096 ? 16 * nst(L) : 4096; }
-TTFSI_HD constexpr int regB_elems(int L) { return 256 * n4_max(L); }
+// shared-memory regions in elements: one chunk's level-4 states at offset 0,
+// one chunk's level-8 states after them; the tile (4096 elements) overlaps
+// both during the Moebius transform; the channels follow.
+TTFSI_HD constexpr int reg4_elems(int L, bool CH) { return 256 * n4c_max(L, CH); }
+TTFSI_HD constexpr int reg8_elems(int L, bool CH) { return 16 * nst(L, CH); }
+TTFSI_HD constexpr int regT_elems(int L, bool CH) {
+    return reg4_elems(L, CH) + reg8_elems(L, CH) > 4096 ? reg4_elems(L, CH) + reg8_elems(L, CH) : 4096;
+}
 
 // channel of (S_L, j = 0) for a 12-bit low set with |S_L| <= L
 TTFSI_HD constexpr int channel_base(int L, int SL) {

@@ -34,10 +34,14 @@ namespace ttfsi {
 //   block 3 (group C): item (sigma_8, u') per thread gathers Z_AB(sigma_8,
 //     u' - |tau_C|; tau_C) and writes the channels Z(sigma_8 u sigma_C, u').
 // Each output state is written by exactly one thread.  States are processed
-// in rounds rd = |sigma_A| (a state's round never changes), so only one
-// round's level-4 and level-8 states are held in shared memory at a time.
-// The kernel is instantiated per order l, which makes every offset and
-// every pruning decision a compile-time constant.
+// in rounds rd = |sigma_A| (a state's round never changes), on the exact
+// path the rounds with 4 or 6 patterns sigma_A in two chunks, so only one
+// chunk's level-4 and level-8 states are held in shared memory at a time
+// (62 KB per CTA at l = 3 with the channels: three CTAs per SM).  The kernel is instantiated
+// per order l, which makes every offset and every pruning decision a
+// compile-time constant; the chunks of a round share one copy of the block
+// 2 and 3 code (the kernel's instruction footprint matters as much as its
+// instruction count: larger unrolled variants lost to instruction fetch).
 //
 // Weighting: the tile, whose high pattern U_H has u_H = |U_H| set bits, forms
 // one partial score per (S_L, s, i) -- i the size of U_H n S_H that a score
@@ -65,6 +69,11 @@ template <typename Acc>
 struct GTraits {
     using G = Acc;
 };
+// Chunked rounds (fast_layout.h) on the exact path, which then fits three
+// CTAs per SM; the float paths keep whole rounds (fewer barriers: float32
+// fits four CTAs per SM either way, float64 is bound by its float64 pipe).
+template <typename Acc>
+constexpr bool kChunked = TileTraits<Acc>::exact;
 template <>
 struct GTraits<long long> {
     using G = __int128;
@@ -130,14 +139,18 @@ __device__ __forceinline__ void zeta16(Acc (&x)[16]) {
         }
 }
 
-// Block 1 of round RD: the level-4 states (sigma_A, t), |sigma_A| = RD, of
-// this thread's position (tau_B, tau_C) from its 16 Moebius values.
-template <int L, int RD, typename Acc>
+// Block 1 of chunk C of round RD: the level-4 states (sigma_A, t),
+// |sigma_A| = RD, rank of sigma_A in the chunk, of this thread's position
+// (tau_B, tau_C) from its 16 Moebius values.
+template <int L, int RD, int C, typename Acc>
 __device__ __forceinline__ void fast_block1(const Acc (&x)[16], Acc *regB, int pos) {
+    constexpr int CA = fast::chunk_a(RD, kChunked<Acc>), A0 = C * CA;
 #pragma unroll
     for (int sg = 0; sg < 16; ++sg) {
         if (fast::pc4(sg) != RD) continue;
-        const int base = fast::rank4(sg) * (5 - RD) - RD;
+        const int ra = fast::rank4(sg);
+        if (ra < A0 || ra >= A0 + CA) continue;
+        const int base = (ra - A0) * (5 - RD) - RD;
 #pragma unroll
         for (int t = RD; t <= 4; ++t) {
             Acc acc = 0;
@@ -149,17 +162,17 @@ __device__ __forceinline__ void fast_block1(const Acc (&x)[16], Acc *regB, int p
     }
 }
 
-// Block 2 item (rank sigma_A = rA, u = RD + uu) of round RD on lane tau_C:
-// gathers the 16 level-4 states Z_A(sigma_A, u - |tau_B|; tau_B), zero where
-// that rank is outside [RD, 4], and writes the level-8 states (sigma_A u
-// sigma_B, u) to regA[tau_C * NST + state].  UU >= 0 fixes uu at compile
-// time, so the zero inputs and the states that cannot exist fold away;
-// UU = -1 takes uu at run time.
+// Block 2 item (rank sigma_A = rA within the chunk, u = RD + uu) of round
+// RD on lane tau_C: gathers the 16 level-4 states Z_A(sigma_A, u - |tau_B|;
+// tau_B), zero where that rank is outside [RD, 4], and writes the level-8
+// states (sigma_A u sigma_B, u) to regA[tau_C * NST + state].  UU >= 0
+// fixes uu at compile time, so the zero inputs and the states that cannot
+// exist fold away; UU = -1 takes uu at run time.
 template <int L, int RD, int UU, typename Acc>
 __device__ __forceinline__ void fast_block2_item(const Acc *regB, Acc *regA, int rA, int uu_rt, int t3) {
     constexpr int O = L - RD;
     constexpr int S8 = fast::s8(L, RD);
-    constexpr int NST = fast::nst(L);
+    constexpr int NST = fast::nst(L, kChunked<Acc>);
     const int uu = UU >= 0 ? UU : uu_rt;
     // input tau_B: level-4 state (sigma_A, t = u - |tau_B|), t in [RD, 4]
     const Acc *src = regB + (rA * (5 - RD) + uu) * 256 + t3;
@@ -182,44 +195,52 @@ __device__ __forceinline__ void fast_block2_item(const Acc *regB, Acc *regA, int
     }
 }
 
-// Block 2 of round RD: items (rank sigma_A, u), u in [RD, 8], 16 lanes over
-// tau_C.  Items run in the order (k, rank sigma_A) with uu = k / 2 for even
-// k and 8 - RD - k / 2 for odd k: the items with uu in {0, 1, 7 - RD, 8 - RD}
-// (at most 5 of their 16 inputs nonzero) come first and run bodies compiled
-// for their uu, and the two half-warps of a warp take the same uu whenever
-// the number of sigma_A is even (for one sigma_A they pair uu with 8 - RD - uu).
+// Block 2 of one chunk of round RD: items (rank sigma_A in the chunk, u),
+// u in [RD, 8], 16 lanes over tau_C, in the order (k, rank sigma_A) with
+// uu = k / 2 for even k and 8 - RD - k / 2 for odd k: the items with uu in
+// {0, 1, 7 - RD, 8 - RD} (at most 5 of their 16 inputs nonzero) come first,
+// and the two half-warps of a warp take the same uu whenever the number of
+// sigma_A is even (for one sigma_A they pair uu with 8 - RD - uu).  On the
+// float paths those items run bodies compiled for their uu (the zero terms
+// fold away, which the float64 pipe needs); the exact path runs one body
+// for every uu (bodies compiled per uu cost it more in instruction fetch
+// than they save).
 template <int L, int RD, typename Acc>
 __device__ __forceinline__ void fast_block2(const Acc *regB, Acc *regA, int tid) {
     constexpr int NU = 9 - RD;
-    constexpr int NA = fast::c4(RD);
+    constexpr int NA = fast::chunk_a(RD, kChunked<Acc>);
     constexpr int NIT = NA * NU;
     const int t3 = tid & 15;
     for (int it = tid >> 4; it < NIT; it += kTileThreads / 16) {
         const int k = it / NA, rA = it - k * NA;
         const int uu = (k & 1) ? NU - 1 - (k >> 1) : (k >> 1);
-        if (uu == 0)
-            fast_block2_item<L, RD, 0>(regB, regA, rA, uu, t3);
-        else if (uu == 1)
-            fast_block2_item<L, RD, 1>(regB, regA, rA, uu, t3);
-        else if (uu == NU - 2)
-            fast_block2_item<L, RD, NU - 2>(regB, regA, rA, uu, t3);
-        else if (uu == NU - 1)
-            fast_block2_item<L, RD, NU - 1>(regB, regA, rA, uu, t3);
-        else
+        if constexpr (TileTraits<Acc>::exact) {
             fast_block2_item<L, RD, -1>(regB, regA, rA, uu, t3);
+        } else {
+            if (uu == 0)
+                fast_block2_item<L, RD, 0>(regB, regA, rA, uu, t3);
+            else if (uu == 1)
+                fast_block2_item<L, RD, 1>(regB, regA, rA, uu, t3);
+            else if (uu == NU - 2)
+                fast_block2_item<L, RD, NU - 2>(regB, regA, rA, uu, t3);
+            else if (uu == NU - 1)
+                fast_block2_item<L, RD, NU - 1>(regB, regA, rA, uu, t3);
+            else
+                fast_block2_item<L, RD, -1>(regB, regA, rA, uu, t3);
+        }
     }
 }
 
 // Block 3 item of round RD, group kB = |sigma_B|: (rank sigma_A, rank
 // sigma_B, u'), u' in [RD + KB, 12]; writes the channels of sigma_8 u sigma_C.
 template <int L, int RD, int KB, typename Acc>
-__device__ __forceinline__ void fast_block3_item(int local, const Acc *regA, Acc *regY) {
+__device__ __forceinline__ void fast_block3_item(int local, const Acc *regA, Acc *regY, int pair0) {
     constexpr int K8 = RD + KB;
     constexpr int O = L - K8;
     constexpr int NU = 13 - K8;
     constexpr int NB = fast::c4(KB);
     constexpr int S8 = fast::s8(L, RD);
-    constexpr int NST = fast::nst(L);
+    constexpr int NST = fast::nst(L, kChunked<Acc>);
     constexpr int OFF8 = fast::off8(RD, KB);
     constexpr int CG = fast::chan_group(L, RD, KB);
     constexpr int CH = fast::ch8(L, K8);
@@ -236,7 +257,7 @@ __device__ __forceinline__ void fast_block3_item(int local, const Acc *regA, Acc
         x[tau] = val;
     }
     zeta16<O>(x);
-    Acc *dst = regY + CG + pair * CH + uu;
+    Acc *dst = regY + CG + (pair0 + pair) * CH + uu;
 #pragma unroll
     for (int sc = 0; sc < 16; ++sc) {
         const int kC = fast::pc4(sc);
@@ -246,54 +267,79 @@ __device__ __forceinline__ void fast_block3_item(int local, const Acc *regA, Acc
     }
 }
 
-// Block 3 of round RD: the groups kB = 0..L-RD one after another, each
-// padded to whole warps so that a warp never mixes two pruning orders.
+// Block 3 of chunk C of round RD: the groups kB = 0..L-RD one after
+// another, each padded to whole warps so that a warp never mixes two
+// pruning orders.  Item pairs are numbered within the chunk; their channels
+// sit at the round's pair index (chunk C starts at pair C * CA * C(4, kB)).
 template <int L, int RD, typename Acc>
-__device__ __forceinline__ void fast_block3(const Acc *regA, Acc *regY, int tid) {
+__device__ __forceinline__ void fast_block3(const Acc *regA, Acc *regY, int tid, int C) {
     constexpr int M = L - RD;
-    constexpr int P0 = fast::pad32(fast::g3(RD, 0));
-    constexpr int P1 = M >= 1 ? fast::pad32(fast::g3(RD, 1)) : 0;
-    constexpr int P2 = M >= 2 ? fast::pad32(fast::g3(RD, 2)) : 0;
-    constexpr int P3 = M >= 3 ? fast::pad32(fast::g3(RD, 3)) : 0;
-    constexpr int P4 = M >= 4 ? fast::pad32(fast::g3(RD, 4)) : 0;
+    constexpr int CA = fast::chunk_a(RD, kChunked<Acc>);
+    constexpr int P0 = fast::pad32(fast::g3(RD, 0, kChunked<Acc>));
+    constexpr int P1 = M >= 1 ? fast::pad32(fast::g3(RD, 1, kChunked<Acc>)) : 0;
+    constexpr int P2 = M >= 2 ? fast::pad32(fast::g3(RD, 2, kChunked<Acc>)) : 0;
+    constexpr int P3 = M >= 3 ? fast::pad32(fast::g3(RD, 3, kChunked<Acc>)) : 0;
+    constexpr int P4 = M >= 4 ? fast::pad32(fast::g3(RD, 4, kChunked<Acc>)) : 0;
     constexpr int TOTAL = P0 + P1 + P2 + P3 + P4;
     for (int it = tid; it < TOTAL; it += kTileThreads) {
         if (it < P0) {
-            if (it < fast::g3(RD, 0)) fast_block3_item<L, RD, 0>(it, regA, regY);
+            if (it < fast::g3(RD, 0, kChunked<Acc>)) fast_block3_item<L, RD, 0>(it, regA, regY, C * CA * fast::c4(0));
         } else if (it < P0 + P1) {
             if constexpr (M >= 1) {
                 const int l = it - P0;
-                if (l < fast::g3(RD, 1)) fast_block3_item<L, RD, 1>(l, regA, regY);
+                if (l < fast::g3(RD, 1, kChunked<Acc>)) fast_block3_item<L, RD, 1>(l, regA, regY, C * CA * fast::c4(1));
             }
         } else if (it < P0 + P1 + P2) {
             if constexpr (M >= 2) {
                 const int l = it - P0 - P1;
-                if (l < fast::g3(RD, 2)) fast_block3_item<L, RD, 2>(l, regA, regY);
+                if (l < fast::g3(RD, 2, kChunked<Acc>)) fast_block3_item<L, RD, 2>(l, regA, regY, C * CA * fast::c4(2));
             }
         } else if (it < P0 + P1 + P2 + P3) {
             if constexpr (M >= 3) {
                 const int l = it - P0 - P1 - P2;
-                if (l < fast::g3(RD, 3)) fast_block3_item<L, RD, 3>(l, regA, regY);
+                if (l < fast::g3(RD, 3, kChunked<Acc>)) fast_block3_item<L, RD, 3>(l, regA, regY, C * CA * fast::c4(3));
             }
         } else {
             if constexpr (M >= 4) {
                 const int l = it - P0 - P1 - P2 - P3;
-                if (l < fast::g3(RD, 4)) fast_block3_item<L, RD, 4>(l, regA, regY);
+                if (l < fast::g3(RD, 4, kChunked<Acc>)) fast_block3_item<L, RD, 4>(l, regA, regY, C * CA * fast::c4(4));
             }
         }
     }
 }
 
-// Round RD: blocks 2 and 3, then block 1 of the next round, which only
-// touches the level-4 region that block 2 has finished reading.
+// Block 1 of chunk C (run time) of round RD.
+template <int L, int RD, typename Acc>
+__device__ __forceinline__ void fast_block1_chunk(const Acc (&x)[16], Acc *regB, int pos, int C) {
+    if constexpr (fast::n_chunks(RD, kChunked<Acc>) == 1) {
+        fast_block1<L, RD, 0>(x, regB, pos);
+    } else {
+        if (C == 0)
+            fast_block1<L, RD, 0>(x, regB, pos);
+        else
+            fast_block1<L, RD, 1>(x, regB, pos);
+    }
+}
+
+// Round RD, chunk by chunk (a run-time loop, so that the chunks share the
+// code of blocks 2 and 3): blocks 2 and 3 of the chunk, then block 1 of the
+// next chunk (of this round or the next), which only touches the level-4
+// region that block 2 has finished reading.
 template <int L, int RD, typename Acc>
 __device__ __forceinline__ void fast_round(const Acc (&x)[16], Acc *regA, Acc *regB, Acc *regY, int tid,
                                            int pos) {
-    fast_block2<L, RD>(regB, regA, tid);
-    __syncthreads();
-    fast_block3<L, RD>(regA, regY, tid);
-    if constexpr (RD < L) fast_block1<L, RD + 1>(x, regB, pos);
-    __syncthreads();
+    constexpr int NC = fast::n_chunks(RD, kChunked<Acc>);
+#pragma unroll 1
+    for (int c = 0; c < NC; ++c) {
+        fast_block2<L, RD>(regB, regA, tid);
+        __syncthreads();
+        fast_block3<L, RD>(regA, regY, tid, c);
+        if (c + 1 < NC)
+            fast_block1_chunk<L, RD>(x, regB, pos, c + 1);
+        else if constexpr (RD < L)
+            fast_block1<L, RD + 1, 0>(x, regB, pos);
+        __syncthreads();
+    }
     if constexpr (RD < L) fast_round<L, RD + 1>(x, regA, regB, regY, tid, pos);
 }
 
@@ -364,13 +410,14 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
     using In = typename TileTraits<Acc>::In;
     using GT = typename GTraits<Acc>::G;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Acc *regA = reinterpret_cast<Acc *>(smem_raw);  // tile, then one round's level-8 states
-    Acc *regB = regA + fast::regA_elems(L);          // one round's level-4 states
-    Acc *regY = regB + fast::regB_elems(L);          // channels
+    Acc *tileS = reinterpret_cast<Acc *>(smem_raw);  // the tile during the Moebius transform
+    Acc *regB = tileS;                                // then one chunk's level-4 states
+    Acc *regA = regB + fast::reg4_elems(L, kChunked<Acc>);  // and one chunk's level-8 states
+    Acc *regY = tileS + fast::regT_elems(L, kChunked<Acc>);  // channels
     using WT = typename WTraits<Acc>::W;
     // this tile's weight rows: the first 16-byte boundary after the channels
     constexpr size_t kWOff =
-        ((size_t)(fast::regA_elems(L) + fast::regB_elems(L) + fast::n_chan(L)) * sizeof(Acc) + 15) & ~(size_t)15;
+        ((size_t)(fast::regT_elems(L, kChunked<Acc>) + fast::n_chan(L)) * sizeof(Acc) + 15) & ~(size_t)15;
     WT *wst = reinterpret_cast<WT *>(smem_raw + kWOff);
     __shared__ int s_emax;
 
@@ -422,16 +469,16 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
     }
     mobius16(x);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) regA[tile_phys(tid + 256 * r)] = x[r];
+    for (int r = 0; r < 16; ++r) tileS[tile_phys(tid + 256 * r)] = x[r];
     __syncthreads();
     // ---- bits 4-7: e = (tid & 15) | r << 4 | (tid >> 4) << 8 ----
     {
         const int e0 = (tid & 15) | ((tid >> 4) << 8);
 #pragma unroll
-        for (int r = 0; r < 16; ++r) x[r] = regA[tile_phys(e0 | (r << 4))];
+        for (int r = 0; r < 16; ++r) x[r] = tileS[tile_phys(e0 | (r << 4))];
         mobius16(x);
 #pragma unroll
-        for (int r = 0; r < 16; ++r) regA[tile_phys(e0 | (r << 4))] = x[r];
+        for (int r = 0; r < 16; ++r) tileS[tile_phys(e0 | (r << 4))] = x[r];
     }
     __syncthreads();
     // ---- bits 0-3: t3 = tid & 15 (tau_C, bits 8-11), t2 = tid >> 4 (tau_B, bits 4-7) ----
@@ -439,12 +486,14 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
     {
         const int e0 = (t2 << 4) | (t3 << 8);
 #pragma unroll
-        for (int r = 0; r < 16; ++r) x[r] = regA[tile_phys(e0 | r)];
+        for (int r = 0; r < 16; ++r) x[r] = tileS[tile_phys(e0 | r)];
         mobius16(x);
     }
+    // the level-4 and level-8 states overwrite the tile
+    __syncthreads();
     // ---- ranked sums: block 1 of round 0, then the rounds ----
     const int pos = t3 + 16 * t2;
-    fast_block1<L, 0>(x, regB, pos);
+    fast_block1<L, 0, 0>(x, regB, pos);
     // the weight rows are read only after this barrier
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
@@ -504,8 +553,14 @@ __device__ __forceinline__ void tile_fast_dispatch(const FastArgs &a, const long
 // One CTA per (tile, game).  CTAs start roughly in linear order, so each asks
 // L2 to prefetch the input of the tile prefetch_ahead CTAs later (about one
 // wave of resident CTAs), which that CTA will then load from L2, not HBM.
+// Resident CTAs per SM the tile kernel is compiled for: three on the
+// chunked exact path at l <= 3 (62 KB of shared memory, at most 80
+// registers), four for float32 at l <= 3, two otherwise.
 template <typename Acc, int L>
-__global__ void __launch_bounds__(kTileThreads, 2) fsi_tile_fast_kernel(FastArgs a) {
+constexpr int kTileMinBlocks = L > 3 ? 2 : TileTraits<Acc>::exact ? 3 : sizeof(Acc) == 4 ? 4 : 2;
+
+template <typename Acc, int L>
+__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks<Acc, L>) fsi_tile_fast_kernel(FastArgs a) {
     using In = typename TileTraits<Acc>::In;
     if (a.prefetch_ahead > 0) {
         const long long lin = (long long)blockIdx.y * gridDim.x + blockIdx.x + a.prefetch_ahead;

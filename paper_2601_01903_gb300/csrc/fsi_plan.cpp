@@ -284,12 +284,14 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
     // fast tile path: shared-memory regions of fast_layout.h
     if (want_fast) {
         if (fast::n_chan(p.ell_eff) != p.n_ch) return TT_FSI_ERR_UNSUPPORTED;  // layouts disagree
-        p.fast_regA = fast::regA_elems(p.ell_eff);
-        p.fast_regB = fast::regB_elems(p.ell_eff);
-        // tile states and channels, then the tile's weight rows (int32 or
-        // int64 on the exact path, the arithmetic's own type otherwise)
+        const bool chunked = arith == TT_FSI_ARITH_EXACT;  // as the kernels' kChunked
+        p.fast_regA = fast::reg8_elems(p.ell_eff, chunked);
+        p.fast_regB = fast::reg4_elems(p.ell_eff, chunked);
+        // tile / chunk states and channels, then the tile's weight rows
+        // (int32 or int64 on the exact path, the arithmetic's own type
+        // otherwise; int32 rows are sized below once the split is decided)
         const size_t wbytes = (arith == TT_FSI_ARITH_F32) ? 4 : 8;
-        p.smem_fast = (size_t)(p.fast_regA + p.fast_regB + p.n_ch) * elem + 16 +
+        p.smem_fast = (size_t)(fast::regT_elems(p.ell_eff, chunked) + p.n_ch) * elem + 16 +
                       (size_t)fast::n_wcombo(p.ell_eff) * fast::kWRow * wbytes;
         p.fast12 = p.smem_fast <= smem_budget;
     }
@@ -435,6 +437,12 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
         p.g_split31 = cmax < (1ll << 31) && yh_max < ((__int128)1 << 31) &&
                       (__int128)13 * cmax * ((__int128)1 << 31) < lim && (__int128)13 * cmax * yh_max < lim;
     }
+
+    // with the split weighting the rows are int32: the shared-memory size
+    // counts them at 4 bytes (three CTAs then share an SM at l <= 3)
+    if (p.fast12 && arith == TT_FSI_ARITH_EXACT && p.g_split31)
+        p.smem_fast = (size_t)(fast::regT_elems(p.ell_eff, true) + p.n_ch) * elem + 16 +
+                      (size_t)fast::n_wcombo(p.ell_eff) * fast::kWRow * 4;
 
     // Weight rows of the fast path per u_H: row (s, |S_L|, i) holds, for
     // j <= 12 - |S_L|, (-1)^(r - i) [omega_s(u_H + r - i, |S_L| + j) + [i = u_H][j = 0]]
