@@ -345,6 +345,128 @@ __global__ void __launch_bounds__(32 * kCombineFastWarps) fsi_combine_fast_kerne
 }
 
 // ----------------------------------------------------------------------------
+// Combine of the split schedule for games of at most 2^12 tiles (exact
+// arithmetic): kC4Lanes lanes per score, each summing every kC4Lanes-th tile
+// (so the lanes of a score read consecutive partial scores), 32 / kC4Lanes
+// scores per warp.  Compared with one warp per score, each lane sums
+// 2^h / kC4Lanes terms in registers and the cross-lane reduction is three
+// shuffle steps, not five; the first batch of partial-score loads is issued
+// before the game's exponent range is known, so the exponent pass overlaps
+// it; the tiles' alignment shifts are computed once per CTA into shared
+// memory and skipped when all tiles of the game share one exponent.  Partial
+// scores come from the previous (tile) launch, so loads may go through L1.
+// Games whose tile exponents span more than shift_cap take the one-warp-per-
+// score routine (its rounding right shifts).
+// ----------------------------------------------------------------------------
+constexpr int kC4Warps = 8;
+constexpr int kC4Lanes = 8;                                // lanes per score
+constexpr int kC4Scores = kC4Warps * (32 / kC4Lanes);     // scores per CTA
+constexpr int kC4MaxTiles = 4096;                          // h <= 12: per-tile shifts in shared memory
+
+__device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
+    unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)((unsigned __int128)v >> 64);
+    lo = __shfl_xor_sync(0xffffffffu, lo, o);
+    hi = __shfl_xor_sync(0xffffffffu, hi, o);
+    return (__int128)(((unsigned __int128)hi << 64) | lo);
+}
+
+template <typename Acc>
+__global__ void __launch_bounds__(32 * kC4Warps, 3) fsi_combine_split_kernel(CombineFastArgs a) {
+    static_assert(TileTraits<Acc>::exact, "exact arithmetic only");
+    using GT = typename GTraits<Acc>::G;
+    constexpr int U = 8;  // partial-score loads in flight per lane
+    __shared__ unsigned char s_shift[kC4MaxTiles];
+    __shared__ int s_fmin, s_fmax;
+    const long long game = a.game0 + blockIdx.y;
+    const int ntile = 1 << a.h;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = lane % kC4Lanes;
+    const long long t_begin = (long long)blockIdx.x * kC4Scores;
+    const long long t_end = t_begin + kC4Scores < a.n_out ? t_begin + kC4Scores : a.n_out;
+    const long long task = t_begin + warp * (32 / kC4Lanes) + lane / kC4Lanes;
+    const bool active = task < t_end;
+    // lanes past the last score stay for the shuffles but sum nothing
+    const long long tk = active ? task : t_begin;
+    const unsigned SH = (unsigned)__ldg(a.tasks + tk * 4 + 1);
+    const int s = __ldg(a.tasks + tk * 4 + 2) & 0xff;
+    const GT *row = reinterpret_cast<const GT *>(a.G) + (game << a.h) * (long long)a.n_g +
+                    (long long)__ldg(a.tasks + tk * 4 + 3) * ntile;
+    const int u_first = active ? q : ntile;
+    auto load_batch = [&](int u0, longlong2 (&raw)[U]) {
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int u = u0 + kC4Lanes * k;
+            raw[k] = u < ntile ? __ldg(reinterpret_cast<const longlong2 *>(
+                                     row + (long long)__popc((unsigned)u & SH) * ntile + u))
+                               : make_longlong2(0, 0);
+        }
+    };
+    longlong2 raw[U];
+    load_batch(u_first, raw);  // in flight during the exponent pass
+
+    const int *texp = a.tile_exp + (game << a.h);
+    int fmin = 0x7fffffff, fmax = -0x7fffffff;
+    for (int u = threadIdx.x; u < ntile; u += blockDim.x) {
+        const int f = __ldg(texp + u);
+        fmin = min(fmin, f);
+        fmax = max(fmax, f);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        fmin = min(fmin, __shfl_xor_sync(0xffffffffu, fmin, o));
+        fmax = max(fmax, __shfl_xor_sync(0xffffffffu, fmax, o));
+    }
+    if (threadIdx.x == 0) {
+        s_fmin = 0x7fffffff;
+        s_fmax = -0x7fffffff;
+    }
+    __syncthreads();
+    if (lane == 0) {
+        atomicMin(&s_fmin, fmin);
+        atomicMax(&s_fmax, fmax);
+    }
+    __syncthreads();
+    const int gmin = s_fmin, gmax = s_fmax;
+    if (gmax - gmin > a.shift_cap) {
+        // rounding right shifts needed: the one-warp-per-score routine
+        combine_fast_body<Acc>(a, game, t_begin, t_end);
+        return;
+    }
+    // every alignment is a left shift by Fc - f in [0, shift_cap], Fc = gmax
+    const bool shifts = gmax != gmin;
+    if (shifts)
+        for (int u = threadIdx.x; u < ntile; u += blockDim.x) s_shift[u] = (unsigned char)(gmax - __ldg(texp + u));
+    __syncthreads();
+    __int128 acc = 0;
+    for (int u0 = u_first;;) {
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const unsigned long long lo = (unsigned long long)raw[k].x;
+            unsigned long long hi = (unsigned long long)raw[k].y, l2 = lo;
+            if (shifts) {
+                const int u = u0 + kC4Lanes * k;
+                const int delta = u < ntile ? s_shift[u] : 0;
+                hi = (hi << delta) | ((lo >> 1) >> (63 - delta));
+                l2 = lo << delta;
+            }
+            acc += (__int128)(((unsigned __int128)hi << 64) | l2);
+        }
+        u0 += kC4Lanes * U;
+        if (u0 >= ntile) break;
+        load_batch(u0, raw);
+    }
+#pragma unroll
+    for (int o = 1; o < kC4Lanes; o <<= 1) acc += shfl_xor_i128(acc, o);
+    if (active && q == 0) {
+        // phi = acc 2^-Fc / D_s (see combine_fast_body)
+        double x, out;
+        if (i128_scaled_to_double(acc, gmax, x))
+            out = x * __ldg(a.winv + s);
+        else
+            out = ldexp(i128_to_double(acc) * __ldg(a.winv + s), -gmax);
+        reinterpret_cast<double *>(a.phi)[game * a.n_out + task] = out;
+    }
+}
+
+// ----------------------------------------------------------------------------
 // Fused apply of a fast-path plan: one persistent launch runs the tiles and
 // the combine of all B games.  Work items come from a device counter in the
 // order T(0), T(1), S(0), T(2), S(1), ..., T(B-1), S(B-2), S(B-1), where T(g)
@@ -825,8 +947,22 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
             cf.shift_cap = p.shift_cap;
             cf.n_out = p.n_out;
             cf.game0 = g0;
-            dim3 g2((unsigned)((p.n_out + kCombineFastWarps - 1) / kCombineFastWarps), (unsigned)nb);
-            fsi_combine_fast_kernel<Acc><<<g2, 32 * kCombineFastWarps, 0, st>>>(cf);
+            // exact arithmetic: any summation order gives the same integers, so
+            // the lane-split combine can replace the fused schedule's routine;
+            // the float paths keep that routine's order (bitwise equal to the
+            // fused schedule)
+            if constexpr (TileTraits<Acc>::exact) {
+                if (p.h <= 12) {
+                    dim3 g2((unsigned)((p.n_out + kC4Scores - 1) / kC4Scores), (unsigned)nb);
+                    fsi_combine_split_kernel<Acc><<<g2, 32 * kC4Warps, 0, st>>>(cf);
+                } else {
+                    dim3 g2((unsigned)((p.n_out + kCombineFastWarps - 1) / kCombineFastWarps), (unsigned)nb);
+                    fsi_combine_fast_kernel<Acc><<<g2, 32 * kCombineFastWarps, 0, st>>>(cf);
+                }
+            } else {
+                dim3 g2((unsigned)((p.n_out + kCombineFastWarps - 1) / kCombineFastWarps), (unsigned)nb);
+                fsi_combine_fast_kernel<Acc><<<g2, 32 * kCombineFastWarps, 0, st>>>(cf);
+            }
         } else {
             dim3 g2((unsigned)p.n_out, (unsigned)nb);
             fsi_combine_kernel<Acc><<<g2, kCombineThreads, 0, st>>>(ca);
