@@ -584,7 +584,7 @@ def run_configs(args, rank, world, local_rank):
         v64 = inputs(key)
         B = v64.shape[0]
         for arith in ("exact", "f64", "f32"):
-            for index in (("fsi", "sii", "bii", "stii") if key == "d20" and ell == 3 else ("fsi",)):
+            for index in (("fsi", "sii", "bii", "stii", "ksii") if key == "d20" and ell == 3 else ("fsi",)):
                 if index != "fsi" and arith == "f64":
                     continue
                 v = v64.float() if arith == "f32" else v64

@@ -96,6 +96,30 @@ __device__ __forceinline__ __int128 mul_wide(long long a, long long b) {
 
 __device__ __forceinline__ int tile_phys(int e) { return e ^ ((e >> 8) & 15); }
 
+// L2 eviction priorities: the input is read once and streams through L2
+// (evict first), the partial scores are read again by the combine launch
+// (evict last), so that they stay in L2 while the input passes.
+__device__ __forceinline__ unsigned long long l2_policy_evict_first() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ unsigned long long l2_policy_evict_last() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ unsigned long long ld_stream_u64(const unsigned long long *ptr, unsigned long long pol) {
+    unsigned long long v;
+    asm volatile("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_keep_i128(__int128 *ptr, __int128 v, unsigned long long pol) {
+    const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)((unsigned __int128)v >> 64);
+    asm volatile("st.global.L2::cache_hint.v2.u64 [%0], {%1, %2}, %3;" ::"l"(ptr), "l"(lo), "l"(hi), "l"(pol)
+                 : "memory");
+}
+
 // Moebius transform over 4 bits, two bits at a time: for the four entries
 // x0..x3 that differ in bits q, q+1 (x3 has both) the result is x0,
 // x1 - x0, x2 - x0 and x3 - x1 - (x2 - x0), i.e. three additions of at most
@@ -438,9 +462,10 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
     if constexpr (TileTraits<Acc>::exact) {
         In raw[16];
         int emax = 0;
+        const unsigned long long pol_in = l2_policy_evict_first();
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
-            raw[r] = __ldg(src + ((tid + 256 * r) & a.load_mask));
+            raw[r] = ld_stream_u64(src + ((tid + 256 * r) & a.load_mask), pol_in);
             emax = max(emax, (int)((raw[r] >> 52) & 0x7ff));
         }
         for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
@@ -503,6 +528,7 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
     // that the combine's lanes (consecutive tiles) read consecutive addresses
     const long long ntile = 1ll << a.h;
     GT *gdst = reinterpret_cast<GT *>(a.G) + (game << a.h) * (long long)a.n_g + tile;
+    const unsigned long long pol_g = l2_policy_evict_last();
     {
         for (int g = tid; g < a.n_g; g += kTileThreads) {
             const int cb = __ldg(a.gtab + 2 * g), code = __ldg(a.gtab + 2 * g + 1);
@@ -531,7 +557,10 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
                     default: acc = fast_g_staged<Acc, 9>(w, regY + cb); break;
                 }
             }
-            gdst[g * ntile] = acc;
+            if constexpr (TileTraits<Acc>::exact)
+                st_keep_i128(gdst + g * ntile, acc, pol_g);
+            else
+                gdst[g * ntile] = acc;
         }
     }
     if constexpr (TileTraits<Acc>::exact) {
@@ -550,9 +579,10 @@ __device__ __forceinline__ void tile_fast_dispatch(const FastArgs &a, const long
     }
 }
 
-// One CTA per (tile, game).  CTAs start roughly in linear order, so each asks
-// L2 to prefetch the input of the tile prefetch_ahead CTAs later (about one
-// wave of resident CTAs), which that CTA will then load from L2, not HBM.
+// One CTA per (tile, game).  With prefetch_ahead > 0 each CTA asks L2 to
+// prefetch the input of the tile prefetch_ahead CTAs later (CTAs start
+// roughly in linear order); the split schedule launches it with 0 (see the
+// launch).
 // Resident CTAs per SM the tile kernel is compiled for: three on the
 // chunked exact path at l <= 3 (62 KB of shared memory, at most 80
 // registers), four for float32 at l <= 3, two otherwise.

@@ -918,7 +918,11 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
             fa.tile_exp = p.d_exp;
             fa.err = p.d_err;
             fa.game0 = g0;
-            fa.prefetch_ahead = p.apply_grid;
+            // no L2 prefetch: with three resident CTAs per SM on the exact
+            // path the other CTAs hide each tile's load, and the prefetch
+            // instructions cost more than they save (distances of 0.66 to 3
+            // waves measured 1 to 3 % slower than none)
+            fa.prefetch_ahead = 0;
             switch (p.ell_eff) {
                 case 1: fsi_tile_fast_kernel<Acc, 1><<<g1, kTileThreads, p.smem_fast, st>>>(fa); break;
                 case 2: fsi_tile_fast_kernel<Acc, 2><<<g1, kTileThreads, p.smem_fast, st>>>(fa); break;
