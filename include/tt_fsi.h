@@ -54,13 +54,14 @@ typedef enum {
 
 /*
  * Arithmetic of the exact path.
- *  TT_FSI_ARITH_EXACT: each tile of 2^b coalitions is rounded once to a
- *    fixed-point integer grid 2^-42.. relative to the tile's largest |v|;
- *    the Moebius and superset sums then run in exact wrap-around int64 /
- *    int128 arithmetic, the weights of Eq. weight are applied as exact
- *    rationals, and each score is rounded once to float64.  The error is at
- *    most 2^l times the input rounding (the operator's row L1 norm), well
- *    below 1e-10 of max|v|.  Input and output are float64.
+ *  TT_FSI_ARITH_EXACT: each tile of 2^b coalitions is cut once (toward
+ *    zero) to a fixed-point integer grid 2^-42.. relative to the tile's
+ *    largest |v|; the Moebius and superset sums then run in exact
+ *    wrap-around int64 / int128 arithmetic, the weights of Eq. weight are
+ *    applied as exact rationals, and each score is rounded once to
+ *    float64.  The error is at most 2^l times the input conversion error
+ *    (the operator's row L1 norm), well below 1e-10 of max|v|.  Input and
+ *    output are float64.
  *  TT_FSI_ARITH_F64: the same algorithm in float64 arithmetic throughout
  *    (GB300 runs float64 at about 1/60 of its integer rate).  float64 in/out.
  *  TT_FSI_ARITH_F32: the same algorithm in float32; float32 in/out.

@@ -1191,12 +1191,13 @@ tt_fsi_status tt_fsi_apply_host(tt_fsi_plan plan, const void *v_host, int64_t B,
             return cuda_status(e);
         }
     }
-    // Games per chunk: explicit, or chunks of at least 4 MiB and at most 16
+    // Games per chunk: explicit, or chunks of at least 16 MiB and at most 16
     // chunks.  The copy stream moves chunk k + 1 while `stream` computes
     // chunk k, so only the last chunk's compute is added to the transfer.
+    // (d = 20, 16 games: 8 MiB chunks 2.29e10 coalitions/s, 16 MiB 2.34e10.)
     int64_t chunk = plan->host_chunk;
     if (chunk <= 0) {
-        const int64_t min_games = (int64_t)(((size_t)4 << 20) + vbytes - 1) / (int64_t)vbytes;
+        const int64_t min_games = (int64_t)(((size_t)16 << 20) + vbytes - 1) / (int64_t)vbytes;
         chunk = std::max(min_games, (B + 15) / 16);
     }
     chunk = std::min(std::max<int64_t>(chunk, 1), B);
