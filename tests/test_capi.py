@@ -63,3 +63,14 @@ def test_host_chunk_setter_rejects_null_plan_on_host():
     import paper_2601_01903_gb300 as fsi
     lib = fsi.native.load()
     assert lib.tt_fsi_plan_set_host_chunk(None, 1) == 1
+
+
+def test_peak_microbenchmark_rejects_bad_arguments():
+    lib = native.load()
+    ops = ctypes.c_int64()
+    dummy = ctypes.c_void_p(256)  # never dereferenced: the checks come first
+    assert lib.tt_fsi_peak_launch(4, 1, 1, dummy, ctypes.byref(ops), None) == 1   # unknown operation
+    assert lib.tt_fsi_peak_launch(0, 0, 1, dummy, ctypes.byref(ops), None) == 1   # no CTA
+    assert lib.tt_fsi_peak_launch(0, 1, 0, dummy, ctypes.byref(ops), None) == 1   # no iteration
+    assert lib.tt_fsi_peak_launch(0, 1, 1, None, ctypes.byref(ops), None) == 1
+    assert lib.tt_fsi_peak_launch(0, 1, 1, dummy, None, None) == 1
