@@ -191,6 +191,17 @@ def test_scale_invariance_of_exact_path(oracle_mod):
     assert _rel_err(got, oracle_mod.fsi(v, d, 2), v) <= TOL
 
 
+@pytest.mark.parametrize("d,ell,B", [(21, 4, 1), (21, 3, 2), (19, 4, 2), (12, 4, 3), (13, 2, 2)])
+def test_scaled_tile_blocks_against_oracle(oracle_mod, d, ell, B):
+    """Games from one tile (d = 12) to 2^9 tiles (d = 21) at orders 2 to 4,
+    with a block of tiles scaled down so that the combine's alignment
+    shifts are not all zero."""
+    v = _noise_games(d, B, seed=d + 13 * ell, v0=False)
+    v[:, : 1 << min(d, 14)] *= 1e-5
+    got, _ = _run(v, d, ell, "exact")
+    assert _rel_err(got, oracle_mod.fsi(v, d, ell), v) <= TOL
+
+
 @pytest.mark.parametrize("d,ell", [(16, 2), (14, 3)])
 def test_tiny_tiles_and_subnormals(oracle_mod, d, ell):
     """A tile whose largest value is below 2^-980 (the exact path's general
