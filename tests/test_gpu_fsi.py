@@ -202,6 +202,32 @@ def test_scaled_tile_blocks_against_oracle(oracle_mod, d, ell, B):
     assert _rel_err(got, oracle_mod.fsi(v, d, ell), v) <= TOL
 
 
+@pytest.mark.parametrize("d,ell,B,scale", [
+    (12, 3, 2, 0), (13, 1, 3, 0), (15, 4, 1, 0), (19, 2, 2, -17), (20, 3, 2, -200),
+    (21, 3, 1, 0), (22, 3, 1, -30), (22, 2, 1, -400),
+])
+def test_split_combine_writes_every_score(oracle_mod, d, ell, B, scale):
+    """Games of 1 to 2^10 tiles through the tile-then-combine schedule:
+    every score is written (the output starts as NaN), bitwise equal to the
+    fused schedule's combine, and within the bar of the oracle -- also with
+    a block of tiles 2^scale below the rest, which beyond the alignment cap
+    takes rounding right shifts."""
+    v = _noise_games(d, B, seed=d * 3 + ell, v0=False)
+    if scale:
+        v[:, : 1 << min(d, 14)] *= 2.0 ** scale
+    vg = _gpu(v)
+    plan = fsi.Plan(d, ell, "exact", max_batch=B)
+    out = torch.full((B, plan.n_scores), float("nan"), dtype=torch.float64, device="cuda")
+    plan.apply(vg, out=out)
+    plan.set_schedule(fused=True)
+    fused = plan.apply(vg)
+    plan.check()
+    assert not torch.isnan(out).any()
+    assert torch.equal(out, fused)
+    ref = oracle_mod.fsi(v, d, ell)
+    assert _rel_err(out.cpu().numpy(), ref, v) <= TOL
+
+
 @pytest.mark.parametrize("d,ell", [(16, 2), (14, 3)])
 def test_tiny_tiles_and_subnormals(oracle_mod, d, ell):
     """A tile whose largest value is below 2^-980 (the exact path's general
