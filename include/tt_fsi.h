@@ -196,24 +196,32 @@ tt_fsi_status tt_fsi_apply(tt_fsi_plan plan, const void *v_dev, int64_t B, void 
                            struct CUstream_st *stream);
 
 /*
- * End-to-end variant of tt_fsi_apply for host-resident data: copies
- * v_host [B, 2^d] to a device staging buffer owned by the plan (allocated on
- * the plan's first tt_fsi_apply_host call, max_batch games in size), runs
- * tt_fsi_apply, copies the scores to phi_host [B, n_scores] and waits for the
- * stream before returning.  The input moves in chunks of whole games on a
- * copy stream owned by the plan, and each chunk is computed on `stream` as
- * soon as it has arrived, so transfer and compute overlap (chunk size:
- * tt_fsi_plan_set_host_chunk).  Results do not depend on the chunking.
- * Page-locked host buffers copy fastest; pageable ones work.  Element types
- * as for tt_fsi_apply.  One call at a time per plan.
+ * End-to-end variant of tt_fsi_apply for host-resident data: v_host [B, 2^d]
+ * in, phi_host [B, n_scores] out, waiting for the stream before returning.
+ * Page-locked input (cudaHostAlloc / cudaHostRegister, e.g. a pinned torch
+ * tensor) is read in place by the tile kernel over the host link, one pass,
+ * no staging copy (unless tt_fsi_plan_set_host_zero_copy(plan, 0)).
+ * Pageable input is copied to a device staging buffer owned by the plan
+ * (allocated on the first call, max_batch games in size) in chunks of whole
+ * games on a copy stream owned by the plan, each chunk computed on `stream`
+ * as soon as it has arrived, so transfer and compute overlap (chunk size:
+ * tt_fsi_plan_set_host_chunk).  The scores go through a plan-owned device
+ * buffer and are copied to phi_host.  Results are bitwise the same on every
+ * route and chunking.  Element types as for tt_fsi_apply.  One call at a
+ * time per plan; v_host must not change until the call returns.
  */
 tt_fsi_status tt_fsi_apply_host(tt_fsi_plan plan, const void *v_host, int64_t B, void *phi_host,
                                 struct CUstream_st *stream);
 
-/* Games per host-transfer chunk of tt_fsi_apply_host: 0 (the default) picks
- * chunks of at least 4 MiB and at most 16 per call; games >= 1 fixes it.
- * TT_FSI_ERR_INVALID_ARG for games < 0. */
+/* Games per host-transfer chunk of the staged route of tt_fsi_apply_host: 0
+ * (the default) picks chunks of at least 16 MiB and at most 16 per call;
+ * games >= 1 fixes it.  TT_FSI_ERR_INVALID_ARG for games < 0. */
 tt_fsi_status tt_fsi_plan_set_host_chunk(tt_fsi_plan plan, int64_t games);
+
+/* enable != 0 (the default): tt_fsi_apply_host reads page-locked input in
+ * place; 0: it always takes the staged copies.  TT_FSI_ERR_INVALID_ARG for a
+ * null plan. */
+tt_fsi_status tt_fsi_plan_set_host_zero_copy(tt_fsi_plan plan, int enable);
 
 /*
  * Tracing.  tt_fsi_plan_profile(plan, 1) makes every later tt_fsi_apply of

@@ -152,6 +152,12 @@ class Plan:
                "tt_fsi_apply_host")
         return out
 
+    def set_host_zero_copy(self, enable: bool = True):
+        """apply_host on page-locked input: read it in place (default) or
+        always through staged copies."""
+        _check(self._lib.tt_fsi_plan_set_host_zero_copy(self._h, 1 if enable else 0),
+               "tt_fsi_plan_set_host_zero_copy")
+
     def set_host_chunk(self, games: int = 0):
         """Games per host-transfer chunk of apply_host (0: automatic)."""
         _check(self._lib.tt_fsi_plan_set_host_chunk(self._h, games), "tt_fsi_plan_set_host_chunk")

@@ -996,6 +996,9 @@ struct tt_fsi_plan_s {
     cudaStream_t s_copy = nullptr;
     cudaEvent_t ev_copy = nullptr;
     int64_t host_chunk = 0;
+    // tt_fsi_apply_host on page-locked input: the tile kernel reads the host
+    // buffer in place (one pass over the host link) instead of a staged copy
+    bool host_zero_copy = true;
 };
 
 namespace {
@@ -1172,6 +1175,18 @@ tt_fsi_status tt_fsi_apply_host(tt_fsi_plan plan, const void *v_host, int64_t B,
     const Plan &p = plan->p;
     const size_t elem = (p.arith == TT_FSI_ARITH_F32) ? 4 : 8;
     const size_t vbytes = ((size_t)1 << p.d) * elem, obytes = (size_t)p.n_out * elem;
+    // Page-locked input: the tile kernel streams it from host memory itself.
+    // It reads every input value exactly once, so the host link carries the
+    // same bytes as a copy would, in one pass and without a staging buffer.
+    const void *v_mapped = nullptr;
+    if (plan->host_zero_copy) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, v_host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+            at.devicePointer != nullptr)
+            v_mapped = at.devicePointer;
+        else
+            cudaGetLastError();  // pageable memory: not an error, take the staged copies
+    }
     if (!plan->d_v_stage) {
         cudaError_t e = cudaMalloc(&plan->d_v_stage, vbytes * (size_t)p.max_batch);
         if (e == cudaSuccess) e = cudaMalloc(&plan->d_phi_stage, obytes * (size_t)p.max_batch);
@@ -1190,6 +1205,14 @@ tt_fsi_status tt_fsi_apply_host(tt_fsi_plan plan, const void *v_host, int64_t B,
             plan->s_copy = nullptr;
             return cuda_status(e);
         }
+    }
+    cudaStream_t st0 = reinterpret_cast<cudaStream_t>(stream);
+    if (v_mapped) {
+        tt_fsi_status s = tt_fsi_apply(plan, v_mapped, B, plan->d_phi_stage, stream);
+        if (s != TT_FSI_OK) return s;
+        cudaError_t e = cudaMemcpyAsync(phi_host, plan->d_phi_stage, obytes * (size_t)B, cudaMemcpyDeviceToHost, st0);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st0);
+        return cuda_status(e);
     }
     // Games per chunk: explicit, or chunks of at least 16 MiB and at most 16
     // chunks.  The copy stream moves chunk k + 1 while `stream` computes
@@ -1223,6 +1246,12 @@ tt_fsi_status tt_fsi_apply_host(tt_fsi_plan plan, const void *v_host, int64_t B,
     e = cudaMemcpyAsync(phi_host, plan->d_phi_stage, obytes * (size_t)B, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return cuda_status(e);
+}
+
+tt_fsi_status tt_fsi_plan_set_host_zero_copy(tt_fsi_plan plan, int enable) {
+    if (!plan) return TT_FSI_ERR_INVALID_ARG;
+    plan->host_zero_copy = enable != 0;
+    return TT_FSI_OK;
 }
 
 tt_fsi_status tt_fsi_plan_set_host_chunk(tt_fsi_plan plan, int64_t games) {

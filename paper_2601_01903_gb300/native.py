@@ -138,6 +138,8 @@ def _declare(lib):
     lib.tt_fsi_apply_host.argtypes = [vp, vp, i64, vp, vp]
     lib.tt_fsi_plan_set_host_chunk.restype = i
     lib.tt_fsi_plan_set_host_chunk.argtypes = [vp, i64]
+    lib.tt_fsi_plan_set_host_zero_copy.restype = i
+    lib.tt_fsi_plan_set_host_zero_copy.argtypes = [vp, i]
     lib.tt_fsi_plan_weights.restype = i
     lib.tt_fsi_plan_weights.argtypes = [i, i, i, vp, vp, vp]
     lib.tt_fsi_plan_profile.restype = i

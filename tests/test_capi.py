@@ -63,6 +63,7 @@ def test_host_chunk_setter_rejects_null_plan_on_host():
     import paper_2601_01903_gb300 as fsi
     lib = fsi.native.load()
     assert lib.tt_fsi_plan_set_host_chunk(None, 1) == 1
+    assert lib.tt_fsi_plan_set_host_zero_copy(None, 1) == 1
 
 
 def test_peak_microbenchmark_rejects_bad_arguments():

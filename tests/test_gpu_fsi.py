@@ -382,16 +382,18 @@ def test_precontracted_sweep_matches_oracle(oracle_mod, arith, d, ell, B):
 
 @pytest.mark.parametrize("arith", ["exact", "f32"])
 @pytest.mark.parametrize("chunk", [0, 1, 3, 7])
-@pytest.mark.parametrize("pinned", [True, False])
-def test_host_pipeline_matches_device_apply(oracle_mod, arith, chunk, pinned):
-    """tt_fsi_apply_host moves the input in chunks of whole games on its own
-    copy stream; every chunking gives the device path's scores bit for bit."""
+@pytest.mark.parametrize("pinned,zero_copy", [(True, True), (True, False), (False, True)])
+def test_host_pipeline_matches_device_apply(oracle_mod, arith, chunk, pinned, zero_copy):
+    """tt_fsi_apply_host reads page-locked input in place, or moves the input
+    in chunks of whole games on its own copy stream; every route and chunking
+    gives the device path's scores bit for bit."""
     d, ell, B = 15, 3, 7
     v = _noise_games(d, B, seed=31)
     dt = torch.float32 if arith == "f32" else torch.float64
     plan = fsi.Plan(d, ell, arith, max_batch=B)
     ref = plan.apply(_gpu(v, dt)).cpu()
     plan.set_host_chunk(chunk)
+    plan.set_host_zero_copy(zero_copy)
     vh = torch.as_tensor(v, dtype=dt)
     if pinned:
         vh = vh.pin_memory()
