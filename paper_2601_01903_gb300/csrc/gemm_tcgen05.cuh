@@ -403,7 +403,11 @@ __global__ void __launch_bounds__(TMA_THREADS) gemm_bf16_tcgen05_tma(const __gri
     auto tileA = [&](int s) { return base + (uint32_t)(s * 2) * TILE_BYTES; };
     auto tileB = [&](int s) { return base + (uint32_t)(s * 2 + 1) * TILE_BYTES; };
 
-    if (threadIdx.x == 0) {
+    // Warp 0 lane 0 produces, warp 1 lane 0 issues the MMAs; the other lanes
+    // of those two warps park at __syncwarp, so no spinning lane of the same
+    // warp competes with the one that does the work.
+    if (warp == 0) {
+        if (lane == 0) {
         // producer
         for (int kb = 0; kb < nk; ++kb) {
             const int s = kb % TMA_STAGES;
@@ -418,7 +422,10 @@ __global__ void __launch_bounds__(TMA_THREADS) gemm_bf16_tcgen05_tma(const __gri
             tma_load_2d(tileA(s), &tmA, k0, m0, smem_u32(&full[s]));
             tma_load_2d(tileB(s), &tmB, k0, n0, smem_u32(&full[s]));
         }
-    } else if (threadIdx.x == 32) {
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
         // MMA issuer
         const uint32_t idesc = instr_desc_bf16(BM, BN);
         bool ok = true;
@@ -439,10 +446,15 @@ __global__ void __launch_bounds__(TMA_THREADS) gemm_bf16_tcgen05_tma(const __gri
         }
         if (!ok) atomicOr(&s_fail, 1);
         mma_commit(smem_u32(&done));  // arrives once every MMA issued above has completed
+        }
+        __syncwarp();
     }
-    // every thread: wait for the accumulator (or the failure flag)
-    const bool ok = mbar_wait(smem_u32(&done), 0);
-    if (!ok) atomicOr(&s_fail, 1);
+    // every warp: lane 0 waits for the accumulator (or the failure flag), the
+    // other lanes wait at the warp barrier without issuing
+    bool done_ok = true;
+    if (lane == 0) done_ok = mbar_wait(smem_u32(&done), 0);
+    __syncwarp();
+    if (lane == 0 && !done_ok) atomicOr(&s_fail, 1);
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!s_fail) {
