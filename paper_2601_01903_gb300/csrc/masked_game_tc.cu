@@ -223,7 +223,10 @@ __global__ void __launch_bounds__(THREADS) masked_game_tc_kernel(Args a) {
                 }
             mma_commit(smem_u32(&mbar));
         }
-        const bool ok = mbar_wait(smem_u32(&mbar), parity);
+        // one lane per warp polls; the others wait at the warp barrier
+        bool ok = true;
+        if ((tid & 31) == 0) ok = mbar_wait(smem_u32(&mbar), parity);
+        __syncwarp();
         parity ^= 1u;
         if (__syncthreads_or(ok ? 0 : 1)) {
             failed = true;
