@@ -153,9 +153,9 @@ constexpr int kErrTimeout = 1;
 // W[r][c] for r < rows_pad (zero for r >= rows; optional), through 32 x 32
 // shared-memory tiles so that the reads and both writes are coalesced.
 // Block 32 x 8 threads, grid (ceil(cols / 32), ceil(rows_pad / 32)).
-__global__ void to_bf16_tiled_kernel(const float *W, int rows, int cols, int rows_pad, bf16 *Wb, bf16 *Wt, int ldt) {
+__device__ __forceinline__ void to_bf16_tile(const float *W, int rows, int cols, int rows_pad, bf16 *Wb, bf16 *Wt,
+                                             int ldt, int c0, int r0) {
     __shared__ float tile[32][33];
-    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
     for (int i = ty; i < 32; i += 8) {
         const int r = r0 + i, c = c0 + tx;
@@ -169,6 +169,29 @@ __global__ void to_bf16_tiled_kernel(const float *W, int rows, int cols, int row
         const int c = c0 + i, r = r0 + tx;
         if (c < cols && r < rows_pad) Wt[(long long)c * ldt + r] = __float2bfloat16_rn(tile[tx][i]);
     }
+}
+
+__global__ void to_bf16_tiled_kernel(const float *W, int rows, int cols, int rows_pad, bf16 *Wb, bf16 *Wt, int ldt) {
+    to_bf16_tile(W, rows, cols, rows_pad, Wb, Wt, ldt, blockIdx.x * 32, blockIdx.y * 32);
+}
+
+// Several casts in one launch: block b takes tile b - first[j] of cast j
+// (the casts' tiles are numbered one after another, column tiles fastest).
+struct CastJob {
+    const float *W;
+    bf16 *Wb, *Wt;
+    int rows, cols, rows_pad, ldt, tiles_x, first;
+};
+struct CastJobs {
+    CastJob j[3];
+    int n;
+};
+__global__ void to_bf16_multi_kernel(CastJobs jobs) {
+    int k = 0;
+    while (k + 1 < jobs.n && (int)blockIdx.x >= jobs.j[k + 1].first) ++k;
+    const CastJob &c = jobs.j[k];
+    const int t = (int)blockIdx.x - c.first;
+    to_bf16_tile(c.W, c.rows, c.cols, c.rows_pad, c.Wb, c.Wt, c.ldt, (t % c.tiles_x) * 32, (t / c.tiles_x) * 32);
 }
 
 // Projection onto sum_{S != empty} phi(S) = target, phi(empty) = v_empty, then
@@ -216,13 +239,16 @@ __global__ void project_loss_kernel(const float *Y, int B, int n_out, const floa
     }
 }
 
-// Column sums of an FP32 [M, N] matrix in a fixed order, in two passes.
-// Pass 1: block (32 columns, a slab of 256 rows), 32 x 8 threads; thread
-// (x, y) sums rows 32y..32y+31 of the slab, the 8 partials are added in order
-// and written to part[slab][N].  Pass 2: one thread per column adds the slab
-// partials in order.
-__global__ void colsum_partial_kernel(const float *X, int M, int N, float *part) {
+// Column sums of an FP32 [M, N] matrix in a fixed order, one launch.  Block
+// (32 columns, a slab of 256 rows), 32 x 8 threads; thread (x, y) sums rows
+// 32y..32y+31 of the slab, the 8 partials are added in order and written to
+// part[slab][N].  The last block to finish a column block (an arrival
+// counter per column block, reset by that block for the next call) adds the
+// slab partials of its 32 columns in slab order.  No block waits for
+// another.
+__global__ void colsum_kernel(const float *X, int M, int N, float *part, int *arrivals, float *out) {
     __shared__ float red[8][33];
+    __shared__ int s_last;
     const int c = blockIdx.x * 32 + threadIdx.x;
     const int r0 = blockIdx.y * 256 + threadIdx.y * 32;
     float s = 0.f;
@@ -232,19 +258,28 @@ __global__ void colsum_partial_kernel(const float *X, int M, int N, float *part)
     }
     red[threadIdx.y][threadIdx.x] = s;
     __syncthreads();
-    if (threadIdx.y == 0 && c < N) {
-        float t = 0.f;
-        for (int k = 0; k < 8; ++k) t += red[k][threadIdx.x];
-        part[(long long)blockIdx.y * N + c] = t;
+    if (threadIdx.y == 0) {
+        if (c < N) {
+            float t = 0.f;
+            for (int k = 0; k < 8; ++k) t += red[k][threadIdx.x];
+            part[(long long)blockIdx.y * N + c] = t;
+        }
+        __threadfence();
     }
-}
-
-__global__ void colsum_final_kernel(const float *part, int slabs, int N, float *out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= N) return;
-    float s = 0.f;
-    for (int k = 0; k < slabs; ++k) s += part[(long long)k * N + c];
-    out[c] = s;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        s_last = atomicAdd(arrivals + blockIdx.x, 1) == (int)gridDim.y - 1;
+    __syncthreads();
+    if (!s_last) return;
+    if (threadIdx.y == 0) {
+        __threadfence();
+        if (c < N) {
+            float t = 0.f;
+            for (int k = 0; k < (int)gridDim.y; ++k) t += __ldcg(part + (long long)k * N + c);
+            out[c] = t;
+        }
+        if (threadIdx.x == 0) arrivals[blockIdx.x] = 0;
+    }
 }
 
 // Sum of the per-instance losses, one block, fixed order.
@@ -314,6 +349,7 @@ struct tt_fsi_student_s {
     float *Z1 = nullptr, *Z2 = nullptr, *Y = nullptr, *dYf = nullptr, *dH2f = nullptr, *dH1f = nullptr;
     float *loss_rows = nullptr;
     float *colpart = nullptr;  // column-sum partials [ceil(max_batch / 256)][max(H, n_out)]
+    int *colarrive = nullptr;  // column-sum arrival counters [ceil(max(H, n_out) / 32)], zero between calls
     float *gpart = nullptr;    // K-slice partial products of the weight gradients
     int *err = nullptr;
     float lr = 1e-3f, beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
@@ -384,15 +420,35 @@ void to_bf16(const float *W, int rows, int cols, int rows_pad, bf16 *Wb, bf16 *W
 // Bias gradient: column sums of an FP32 [M, N] matrix (fixed order).
 void colsum(tt_fsi_student_s *s, const float *X, int M, int N, float *out, cudaStream_t st) {
     const int slabs = (M + 255) / 256;
-    ttfsi_student::colsum_partial_kernel<<<dim3((unsigned)((N + 31) / 32), (unsigned)slabs), dim3(32, 8), 0, st>>>(
-        X, M, N, s->colpart);
-    ttfsi_student::colsum_final_kernel<<<(N + 127) / 128, 128, 0, st>>>(s->colpart, slabs, N, out);
+    ttfsi_student::colsum_kernel<<<dim3((unsigned)((N + 31) / 32), (unsigned)slabs), dim3(32, 8), 0, st>>>(
+        X, M, N, s->colpart, s->colarrive, out);
 }
 
+// BF16 copies of the three weight matrices (and the transposes the backward
+// pass reads), one launch.
 tt_fsi_status refresh_bf16(tt_fsi_student_s *s, cudaStream_t st) {
-    to_bf16(s->params + s->off_W1, s->H, s->d, s->H, s->W1b, nullptr, 0, st);
-    to_bf16(s->params + s->off_W2, s->H, s->H, s->H, s->W2b, s->W2bT, s->H, st);
-    to_bf16(s->params + s->off_W3, s->n_out, s->H, s->n_pad, s->W3b, s->W3bT, s->n_pad, st);
+    using ttfsi_student::CastJob;
+    ttfsi_student::CastJobs jobs{};
+    auto add = [&](const float *W, int rows, int cols, int rows_pad, bf16 *Wb, bf16 *Wt, int ldt) {
+        CastJob &c = jobs.j[jobs.n];
+        c.W = W;
+        c.Wb = Wb;
+        c.Wt = Wt;
+        c.rows = rows;
+        c.cols = cols;
+        c.rows_pad = rows_pad;
+        c.ldt = ldt;
+        c.tiles_x = (cols + 31) / 32;
+        c.first = jobs.n ? jobs.j[jobs.n - 1].first + jobs.j[jobs.n - 1].tiles_x * ((jobs.j[jobs.n - 1].rows_pad + 31) / 32)
+                         : 0;
+        ++jobs.n;
+    };
+    add(s->params + s->off_W1, s->H, s->d, s->H, s->W1b, nullptr, 0);
+    add(s->params + s->off_W2, s->H, s->H, s->H, s->W2b, s->W2bT, s->H);
+    add(s->params + s->off_W3, s->n_out, s->H, s->n_pad, s->W3b, s->W3bT, s->n_pad);
+    const CastJob &last = jobs.j[jobs.n - 1];
+    const unsigned blocks = (unsigned)(last.first + last.tiles_x * ((last.rows_pad + 31) / 32));
+    ttfsi_student::to_bf16_multi_kernel<<<blocks, dim3(32, 8), 0, st>>>(jobs);
     return st_status(cudaGetLastError());
 }
 
@@ -520,6 +576,7 @@ tt_fsi_status tt_fsi_student_create(int d, int hidden, int n_out, int max_batch,
     A(&s->dH1T, H * Bm);
     A(&s->loss_rows, Bm);
     A(&s->colpart, ((Bm + 255) / 256) * (size_t)std::max(hidden, n_out));
+    A(&s->colarrive, ((size_t)std::max(hidden, n_out) + 31) / 32);
     {
         // the largest split product: the weight gradients W3 [n_out, H], W2 [H, H], W1 [H, d] with
         // K = max_batch
