@@ -592,6 +592,9 @@ constexpr int kTileMinBlocks = L > 3 ? 2 : TileTraits<Acc>::exact ? 3 : sizeof(A
 template <typename Acc, int L>
 __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks<Acc, L>) fsi_tile_fast_kernel(FastArgs a) {
     using In = typename TileTraits<Acc>::In;
+    // a combine launched as this grid's programmatic dependent may be placed
+    // on the SMs from now on; it waits for this grid's results before reading
+    asm volatile("griddepcontrol.launch_dependents;");
     if (a.prefetch_ahead > 0) {
         const long long lin = (long long)blockIdx.y * gridDim.x + blockIdx.x + a.prefetch_ahead;
         if (lin < (long long)gridDim.x * gridDim.y) {

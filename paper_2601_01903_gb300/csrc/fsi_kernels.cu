@@ -339,6 +339,9 @@ __device__ __forceinline__ void combine_fast_body(const CombineFastArgs &a, cons
 
 template <typename Acc>
 __global__ void __launch_bounds__(32 * kCombineFastWarps) fsi_combine_fast_kernel(CombineFastArgs a) {
+    // as the tile launch's programmatic dependent: wait for its results
+    // (returns at once otherwise); combine_fast_body reads them past L1
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const long long t0 = (long long)blockIdx.x * kCombineFastWarps;
     const long long t1 = (t0 + kCombineFastWarps < a.n_out) ? t0 + kCombineFastWarps : a.n_out;
     combine_fast_body<Acc>(a, a.game0 + blockIdx.y, t0, t1);
@@ -375,6 +378,10 @@ __global__ void __launch_bounds__(32 * kC4Warps, 3) fsi_combine_split_kernel(Com
     static_assert(TileTraits<Acc>::exact, "exact arithmetic only");
     using GT = typename GTraits<Acc>::G;
     constexpr int U = 8;  // partial-score loads in flight per lane
+    // launched as the tile grid's programmatic dependent: wait until that
+    // grid has finished and its partial scores and exponents are visible
+    // (returns at once otherwise); they are read past L1 (ld.global.cg)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     __shared__ unsigned char s_shift[kC4MaxTiles];
     __shared__ int s_fmin, s_fmax;
     const long long game = a.game0 + blockIdx.y;
@@ -395,7 +402,7 @@ __global__ void __launch_bounds__(32 * kC4Warps, 3) fsi_combine_split_kernel(Com
 #pragma unroll
         for (int k = 0; k < U; ++k) {
             const int u = u0 + kC4Lanes * k;
-            raw[k] = u < ntile ? __ldg(reinterpret_cast<const longlong2 *>(
+            raw[k] = u < ntile ? __ldcg(reinterpret_cast<const longlong2 *>(
                                      row + (long long)__popc((unsigned)u & SH) * ntile + u))
                                : make_longlong2(0, 0);
         }
@@ -406,7 +413,7 @@ __global__ void __launch_bounds__(32 * kC4Warps, 3) fsi_combine_split_kernel(Com
     const int *texp = a.tile_exp + (game << a.h);
     int fmin = 0x7fffffff, fmax = -0x7fffffff;
     for (int u = threadIdx.x; u < ntile; u += blockDim.x) {
-        const int f = __ldg(texp + u);
+        const int f = __ldcg(texp + u);
         fmin = min(fmin, f);
         fmax = max(fmax, f);
     }
@@ -433,7 +440,7 @@ __global__ void __launch_bounds__(32 * kC4Warps, 3) fsi_combine_split_kernel(Com
     // every alignment is a left shift by Fc - f in [0, shift_cap], Fc = gmax
     const bool shifts = gmax != gmin;
     if (shifts)
-        for (int u = threadIdx.x; u < ntile; u += blockDim.x) s_shift[u] = (unsigned char)(gmax - __ldg(texp + u));
+        for (int u = threadIdx.x; u < ntile; u += blockDim.x) s_shift[u] = (unsigned char)(gmax - __ldcg(texp + u));
     __syncthreads();
     __int128 acc = 0;
     for (int u0 = u_first;;) {
@@ -824,6 +831,25 @@ cudaError_t fused_grid(const Plan &p, int *grid) {
     return e;
 }
 
+// Launches a combine kernel as the programmatic dependent of the tile
+// launch just before it on `st`: its CTAs may be placed while the tile grid
+// drains, and each waits in the kernel (griddepcontrol.wait) for the tile
+// grid's results before reading them.
+template <typename Args>
+cudaError_t launch_dependent(void (*kernel)(Args), dim3 grid, dim3 block, cudaStream_t st, const Args &args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args);
+}
+
 template <typename Acc>
 tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, cudaStream_t st,
                            cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,
@@ -958,14 +984,17 @@ tt_fsi_status launch_apply(const Plan &p, const void *v, int64_t B, void *phi, c
             if constexpr (TileTraits<Acc>::exact) {
                 if (p.h <= 12) {
                     dim3 g2((unsigned)((p.n_out + kC4Scores - 1) / kC4Scores), (unsigned)nb);
-                    fsi_combine_split_kernel<Acc><<<g2, 32 * kC4Warps, 0, st>>>(cf);
+                    cudaError_t le = launch_dependent(fsi_combine_split_kernel<Acc>, g2, dim3(32 * kC4Warps), st, cf);
+                    if (le != cudaSuccess) return cuda_status(le);
                 } else {
                     dim3 g2((unsigned)((p.n_out + kCombineFastWarps - 1) / kCombineFastWarps), (unsigned)nb);
-                    fsi_combine_fast_kernel<Acc><<<g2, 32 * kCombineFastWarps, 0, st>>>(cf);
+                    cudaError_t le = launch_dependent(fsi_combine_fast_kernel<Acc>, g2, dim3(32 * kCombineFastWarps), st, cf);
+                    if (le != cudaSuccess) return cuda_status(le);
                 }
             } else {
                 dim3 g2((unsigned)((p.n_out + kCombineFastWarps - 1) / kCombineFastWarps), (unsigned)nb);
-                fsi_combine_fast_kernel<Acc><<<g2, 32 * kCombineFastWarps, 0, st>>>(cf);
+                cudaError_t le = launch_dependent(fsi_combine_fast_kernel<Acc>, g2, dim3(32 * kCombineFastWarps), st, cf);
+                if (le != cudaSuccess) return cuda_status(le);
             }
         } else {
             dim3 g2((unsigned)p.n_out, (unsigned)nb);
