@@ -460,11 +460,13 @@ tt_fsi_status forward(tt_fsi_student_s *s, const float *x, int B, bool train, cu
     tt_fsi_status r = st_status(cudaGetLastError());
     if (r != TT_FSI_OK) return r;
     const float *P = s->params;
-    r = gemm(s->Xb, s->d, s->W1b, s->d, B, s->H, s->d, P + s->off_b1, 1, nullptr, 0, s->Z1, s->H, s->A1, s->H,
-             train ? s->A1T : nullptr, s->ldB, s->err, st);
+    // the FP32 pre-activations Z1, Z2 and the transposed activations are
+    // read only by the backward pass
+    r = gemm(s->Xb, s->d, s->W1b, s->d, B, s->H, s->d, P + s->off_b1, 1, nullptr, 0, train ? s->Z1 : nullptr, s->H,
+             s->A1, s->H, train ? s->A1T : nullptr, s->ldB, s->err, st);
     if (r != TT_FSI_OK) return r;
-    r = gemm(s->A1, s->H, s->W2b, s->H, B, s->H, s->H, P + s->off_b2, 1, nullptr, 0, s->Z2, s->H, s->A2, s->H,
-             train ? s->A2T : nullptr, s->ldB, s->err, st);
+    r = gemm(s->A1, s->H, s->W2b, s->H, B, s->H, s->H, P + s->off_b2, 1, nullptr, 0, train ? s->Z2 : nullptr, s->H,
+             s->A2, s->H, train ? s->A2T : nullptr, s->ldB, s->err, st);
     if (r != TT_FSI_OK) return r;
     return gemm(s->A2, s->H, s->W3b, s->H, B, s->n_out, s->H, P + s->off_b3, 0, nullptr, 0, s->Y, s->n_out, nullptr, 0,
                 nullptr, 0, s->err, st, s->gpart);
