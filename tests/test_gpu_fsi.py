@@ -285,6 +285,28 @@ def test_repeated_calls_are_bitwise_identical():
 
 
 @pytest.mark.parametrize("arith", ["exact", "f64", "f32"])
+def test_back_to_back_calls_with_different_inputs(arith):
+    """The combine is launched as the tile launch's programmatic dependent;
+    calls enqueued back to back on one stream with different inputs, and no
+    host sync between them, must each see only their own partial scores."""
+    d, ell, B = 18, 3, 3
+    dt = torch.float32 if arith == "f32" else torch.float64
+    vs = [_gpu(_noise_games(d, B, seed=60 + k), dt) for k in range(3)]
+    plan = fsi.Plan(d, ell, arith, max_batch=B)
+    refs = [plan.apply(v).clone() for v in vs]
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    outs = [torch.empty_like(refs[0]) for _ in range(12)]
+    with torch.cuda.stream(s):
+        for i in range(12):
+            plan.apply(vs[i % 3], out=outs[i], stream=s)
+    s.synchronize()
+    plan.check()
+    for i in range(12):
+        assert torch.equal(outs[i], refs[i % 3])
+
+
+@pytest.mark.parametrize("arith", ["exact", "f64", "f32"])
 @pytest.mark.parametrize("d,ell,B", [(14, 3, 5), (20, 2, 2), (9, 3, 7), (16, 1, 3), (13, 3, 1), (17, 4, 2)])
 def test_fused_schedule_matches_two_launches(arith, d, ell, B):
     """The fused persistent launch and the tile-then-combine launches run the
