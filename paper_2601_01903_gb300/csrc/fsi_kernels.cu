@@ -383,6 +383,7 @@ __global__ void __launch_bounds__(32 * kC4Warps, 3) fsi_combine_split_kernel(Com
     // (returns at once otherwise); they are read past L1 (ld.global.cg)
     asm volatile("griddepcontrol.wait;" ::: "memory");
     __shared__ unsigned char s_shift[kC4MaxTiles];
+    __shared__ int s_f[kC4MaxTiles];  // the game's tile exponents
     __shared__ int s_fmin, s_fmax;
     const long long game = a.game0 + blockIdx.y;
     const int ntile = 1 << a.h;
@@ -414,6 +415,7 @@ __global__ void __launch_bounds__(32 * kC4Warps, 3) fsi_combine_split_kernel(Com
     int fmin = 0x7fffffff, fmax = -0x7fffffff;
     for (int u = threadIdx.x; u < ntile; u += blockDim.x) {
         const int f = __ldcg(texp + u);
+        s_f[u] = f;  // kept for the shift table (no second trip to L2)
         fmin = min(fmin, f);
         fmax = max(fmax, f);
     }
@@ -440,7 +442,7 @@ __global__ void __launch_bounds__(32 * kC4Warps, 3) fsi_combine_split_kernel(Com
     // every alignment is a left shift by Fc - f in [0, shift_cap], Fc = gmax
     const bool shifts = gmax != gmin;
     if (shifts)
-        for (int u = threadIdx.x; u < ntile; u += blockDim.x) s_shift[u] = (unsigned char)(gmax - __ldcg(texp + u));
+        for (int u = threadIdx.x; u < ntile; u += blockDim.x) s_shift[u] = (unsigned char)(gmax - s_f[u]);
     __syncthreads();
     __int128 acc = 0;
     for (int u0 = u_first;;) {
