@@ -38,12 +38,16 @@ TTFSI_HD constexpr int n4(int rd) { return c4(rd) * (5 - rd); }
 
 // A round's states can be processed in chunks of consecutive ranks of
 // sigma_A, so that only one chunk's level-4 and level-8 states are held in
-// shared memory at a time: with CH (chunked) the rounds with 4 or 6
-// patterns sigma_A (rd = 1, 2) in two chunks, the others whole; without,
-// every round whole.
-TTFSI_HD constexpr int n_chunks(int rd, bool CH) { return CH && (rd == 1 || rd == 2) ? 2 : 1; }
-TTFSI_HD constexpr int chunk_a(int rd, bool CH) { return c4(rd) / n_chunks(rd, CH); }
-TTFSI_HD constexpr int n4c_max(int L, bool CH) {
+// shared memory at a time.  Chunk mode CH: 0, every round whole; 1, the
+// rounds with 4 or 6 patterns sigma_A (rd = 1, 2) in two chunks; 2, round 1
+// in two chunks and round 2 in three, so that a chunk's block-2 items
+// (patterns x ranks: 16 and 14) fit one pass of a CTA's 16 half-warps.
+// Mode 2 never needs more shared memory than mode 1.
+TTFSI_HD constexpr int n_chunks(int rd, int CH) {
+    return CH == 0 ? 1 : rd == 1 ? 2 : rd == 2 ? (CH == 2 ? 3 : 2) : 1;
+}
+TTFSI_HD constexpr int chunk_a(int rd, int CH) { return c4(rd) / n_chunks(rd, CH); }
+TTFSI_HD constexpr int n4c_max(int L, int CH) {
     int m = 0;
     for (int rd = 0; rd <= L; ++rd) m = chunk_a(rd, CH) * (5 - rd) > m ? chunk_a(rd, CH) * (5 - rd) : m;
     return m;
@@ -59,7 +63,7 @@ TTFSI_HD constexpr int s8(int L, int rd) { return off8(rd, L - rd + 1); }
 // Row stride of the level-8 region [tau_C][state]: the largest chunk, made
 // odd so that both the writes (16 tau_C, one state) and the reads (one
 // tau_C, consecutive states) fall on distinct 8-byte bank pairs.
-TTFSI_HD constexpr int nst(int L, bool CH) {
+TTFSI_HD constexpr int nst(int L, int CH) {
     int m = 0;
     for (int rd = 0; rd <= L; ++rd) m = chunk_a(rd, CH) * s8(L, rd) > m ? chunk_a(rd, CH) * s8(L, rd) : m;
     return m | 1;
@@ -84,15 +88,15 @@ TTFSI_HD constexpr int n_chan(int L) { return chan_group(L, L + 1, 0); }
 
 // block-3 items of one chunk of round rd and group kB: (rank sigma_A,
 // rank sigma_B, u'), u' in [rd + kB, 12]; each group padded to whole warps
-TTFSI_HD constexpr int g3(int rd, int kB, bool CH) { return chunk_a(rd, CH) * c4(kB) * (13 - rd - kB); }
+TTFSI_HD constexpr int g3(int rd, int kB, int CH) { return chunk_a(rd, CH) * c4(kB) * (13 - rd - kB); }
 TTFSI_HD constexpr int pad32(int n) { return (n + 31) & ~31; }
 
 // shared-memory regions in elements: one chunk's level-4 states at offset 0,
 // one chunk's level-8 states after them; the tile (4096 elements) overlaps
 // both during the Moebius transform; the channels follow.
-TTFSI_HD constexpr int reg4_elems(int L, bool CH) { return 256 * n4c_max(L, CH); }
-TTFSI_HD constexpr int reg8_elems(int L, bool CH) { return 16 * nst(L, CH); }
-TTFSI_HD constexpr int regT_elems(int L, bool CH) {
+TTFSI_HD constexpr int reg4_elems(int L, int CH) { return 256 * n4c_max(L, CH); }
+TTFSI_HD constexpr int reg8_elems(int L, int CH) { return 16 * nst(L, CH); }
+TTFSI_HD constexpr int regT_elems(int L, int CH) {
     return reg4_elems(L, CH) + reg8_elems(L, CH) > 4096 ? reg4_elems(L, CH) + reg8_elems(L, CH) : 4096;
 }
 

@@ -73,7 +73,14 @@ struct GTraits {
 // CTAs per SM; the float paths keep whole rounds (fewer barriers: float32
 // fits four CTAs per SM either way, float64 is bound by its float64 pipe).
 template <typename Acc>
-constexpr bool kChunked = TileTraits<Acc>::exact;
+constexpr int kChunked = TileTraits<Acc>::exact ? 1 : 0;
+// The tile launch (fsi_tile_fast_kernel) runs round 2 in three chunks
+// (fast_layout.h, mode 2): one pass of block 2 per chunk.  The persistent
+// kernels, which carry the combine as well, keep mode 1 (two chunks), which
+// measured faster for them.  Mode 2 needs no more shared memory than mode 1,
+// so the plan sizes every launch by mode 1.
+template <typename Acc>
+constexpr int kTileChunkMode = TileTraits<Acc>::exact ? 2 : 0;
 template <>
 struct GTraits<long long> {
     using G = __int128;
@@ -166,9 +173,9 @@ __device__ __forceinline__ void zeta16(Acc (&x)[16]) {
 // Block 1 of chunk C of round RD: the level-4 states (sigma_A, t),
 // |sigma_A| = RD, rank of sigma_A in the chunk, of this thread's position
 // (tau_B, tau_C) from its 16 Moebius values.
-template <int L, int RD, int C, typename Acc>
+template <int L, int RD, int C, int CM, typename Acc>
 __device__ __forceinline__ void fast_block1(const Acc (&x)[16], Acc *regB, int pos) {
-    constexpr int CA = fast::chunk_a(RD, kChunked<Acc>), A0 = C * CA;
+    constexpr int CA = fast::chunk_a(RD, CM), A0 = C * CA;
 #pragma unroll
     for (int sg = 0; sg < 16; ++sg) {
         if (fast::pc4(sg) != RD) continue;
@@ -192,11 +199,11 @@ __device__ __forceinline__ void fast_block1(const Acc (&x)[16], Acc *regB, int p
 // states (sigma_A u sigma_B, u) to regA[tau_C * NST + state].  UU >= 0
 // fixes uu at compile time, so the zero inputs and the states that cannot
 // exist fold away; UU = -1 takes uu at run time.
-template <int L, int RD, int UU, typename Acc>
+template <int L, int RD, int UU, int CM, typename Acc>
 __device__ __forceinline__ void fast_block2_item(const Acc *regB, Acc *regA, int rA, int uu_rt, int t3) {
     constexpr int O = L - RD;
     constexpr int S8 = fast::s8(L, RD);
-    constexpr int NST = fast::nst(L, kChunked<Acc>);
+    constexpr int NST = fast::nst(L, CM);
     const int uu = UU >= 0 ? UU : uu_rt;
     // input tau_B: level-4 state (sigma_A, t = u - |tau_B|), t in [RD, 4]
     const Acc *src = regB + (rA * (5 - RD) + uu) * 256 + t3;
@@ -229,42 +236,42 @@ __device__ __forceinline__ void fast_block2_item(const Acc *regB, Acc *regA, int
 // fold away, which the float64 pipe needs); the exact path runs one body
 // for every uu (bodies compiled per uu cost it more in instruction fetch
 // than they save).
-template <int L, int RD, typename Acc>
+template <int L, int RD, int CM, typename Acc>
 __device__ __forceinline__ void fast_block2(const Acc *regB, Acc *regA, int tid) {
     constexpr int NU = 9 - RD;
-    constexpr int NA = fast::chunk_a(RD, kChunked<Acc>);
+    constexpr int NA = fast::chunk_a(RD, CM);
     constexpr int NIT = NA * NU;
     const int t3 = tid & 15;
     for (int it = tid >> 4; it < NIT; it += kTileThreads / 16) {
         const int k = it / NA, rA = it - k * NA;
         const int uu = (k & 1) ? NU - 1 - (k >> 1) : (k >> 1);
         if constexpr (TileTraits<Acc>::exact) {
-            fast_block2_item<L, RD, -1>(regB, regA, rA, uu, t3);
+            fast_block2_item<L, RD, -1, CM>(regB, regA, rA, uu, t3);
         } else {
             if (uu == 0)
-                fast_block2_item<L, RD, 0>(regB, regA, rA, uu, t3);
+                fast_block2_item<L, RD, 0, CM>(regB, regA, rA, uu, t3);
             else if (uu == 1)
-                fast_block2_item<L, RD, 1>(regB, regA, rA, uu, t3);
+                fast_block2_item<L, RD, 1, CM>(regB, regA, rA, uu, t3);
             else if (uu == NU - 2)
-                fast_block2_item<L, RD, NU - 2>(regB, regA, rA, uu, t3);
+                fast_block2_item<L, RD, NU - 2, CM>(regB, regA, rA, uu, t3);
             else if (uu == NU - 1)
-                fast_block2_item<L, RD, NU - 1>(regB, regA, rA, uu, t3);
+                fast_block2_item<L, RD, NU - 1, CM>(regB, regA, rA, uu, t3);
             else
-                fast_block2_item<L, RD, -1>(regB, regA, rA, uu, t3);
+                fast_block2_item<L, RD, -1, CM>(regB, regA, rA, uu, t3);
         }
     }
 }
 
 // Block 3 item of round RD, group kB = |sigma_B|: (rank sigma_A, rank
 // sigma_B, u'), u' in [RD + KB, 12]; writes the channels of sigma_8 u sigma_C.
-template <int L, int RD, int KB, typename Acc>
+template <int L, int RD, int KB, int CM, typename Acc>
 __device__ __forceinline__ void fast_block3_item(int local, const Acc *regA, Acc *regY, int pair0) {
     constexpr int K8 = RD + KB;
     constexpr int O = L - K8;
     constexpr int NU = 13 - K8;
     constexpr int NB = fast::c4(KB);
     constexpr int S8 = fast::s8(L, RD);
-    constexpr int NST = fast::nst(L, kChunked<Acc>);
+    constexpr int NST = fast::nst(L, CM);
     constexpr int OFF8 = fast::off8(RD, KB);
     constexpr int CG = fast::chan_group(L, RD, KB);
     constexpr int CH = fast::ch8(L, K8);
@@ -295,53 +302,62 @@ __device__ __forceinline__ void fast_block3_item(int local, const Acc *regA, Acc
 // another, each padded to whole warps so that a warp never mixes two
 // pruning orders.  Item pairs are numbered within the chunk; their channels
 // sit at the round's pair index (chunk C starts at pair C * CA * C(4, kB)).
-template <int L, int RD, typename Acc>
+template <int L, int RD, int CM, typename Acc>
 __device__ __forceinline__ void fast_block3(const Acc *regA, Acc *regY, int tid, int C) {
     constexpr int M = L - RD;
-    constexpr int CA = fast::chunk_a(RD, kChunked<Acc>);
-    constexpr int P0 = fast::pad32(fast::g3(RD, 0, kChunked<Acc>));
-    constexpr int P1 = M >= 1 ? fast::pad32(fast::g3(RD, 1, kChunked<Acc>)) : 0;
-    constexpr int P2 = M >= 2 ? fast::pad32(fast::g3(RD, 2, kChunked<Acc>)) : 0;
-    constexpr int P3 = M >= 3 ? fast::pad32(fast::g3(RD, 3, kChunked<Acc>)) : 0;
-    constexpr int P4 = M >= 4 ? fast::pad32(fast::g3(RD, 4, kChunked<Acc>)) : 0;
+    constexpr int CA = fast::chunk_a(RD, CM);
+    constexpr int P0 = fast::pad32(fast::g3(RD, 0, CM));
+    constexpr int P1 = M >= 1 ? fast::pad32(fast::g3(RD, 1, CM)) : 0;
+    constexpr int P2 = M >= 2 ? fast::pad32(fast::g3(RD, 2, CM)) : 0;
+    constexpr int P3 = M >= 3 ? fast::pad32(fast::g3(RD, 3, CM)) : 0;
+    constexpr int P4 = M >= 4 ? fast::pad32(fast::g3(RD, 4, CM)) : 0;
     constexpr int TOTAL = P0 + P1 + P2 + P3 + P4;
     for (int it = tid; it < TOTAL; it += kTileThreads) {
         if (it < P0) {
-            if (it < fast::g3(RD, 0, kChunked<Acc>)) fast_block3_item<L, RD, 0>(it, regA, regY, C * CA * fast::c4(0));
+            if (it < fast::g3(RD, 0, CM)) fast_block3_item<L, RD, 0, CM>(it, regA, regY, C * CA * fast::c4(0));
         } else if (it < P0 + P1) {
             if constexpr (M >= 1) {
                 const int l = it - P0;
-                if (l < fast::g3(RD, 1, kChunked<Acc>)) fast_block3_item<L, RD, 1>(l, regA, regY, C * CA * fast::c4(1));
+                if (l < fast::g3(RD, 1, CM)) fast_block3_item<L, RD, 1, CM>(l, regA, regY, C * CA * fast::c4(1));
             }
         } else if (it < P0 + P1 + P2) {
             if constexpr (M >= 2) {
                 const int l = it - P0 - P1;
-                if (l < fast::g3(RD, 2, kChunked<Acc>)) fast_block3_item<L, RD, 2>(l, regA, regY, C * CA * fast::c4(2));
+                if (l < fast::g3(RD, 2, CM)) fast_block3_item<L, RD, 2, CM>(l, regA, regY, C * CA * fast::c4(2));
             }
         } else if (it < P0 + P1 + P2 + P3) {
             if constexpr (M >= 3) {
                 const int l = it - P0 - P1 - P2;
-                if (l < fast::g3(RD, 3, kChunked<Acc>)) fast_block3_item<L, RD, 3>(l, regA, regY, C * CA * fast::c4(3));
+                if (l < fast::g3(RD, 3, CM)) fast_block3_item<L, RD, 3, CM>(l, regA, regY, C * CA * fast::c4(3));
             }
         } else {
             if constexpr (M >= 4) {
                 const int l = it - P0 - P1 - P2 - P3;
-                if (l < fast::g3(RD, 4, kChunked<Acc>)) fast_block3_item<L, RD, 4>(l, regA, regY, C * CA * fast::c4(4));
+                if (l < fast::g3(RD, 4, CM)) fast_block3_item<L, RD, 4, CM>(l, regA, regY, C * CA * fast::c4(4));
             }
         }
     }
 }
 
 // Block 1 of chunk C (run time) of round RD.
-template <int L, int RD, typename Acc>
+template <int L, int RD, int CM, typename Acc>
 __device__ __forceinline__ void fast_block1_chunk(const Acc (&x)[16], Acc *regB, int pos, int C) {
-    if constexpr (fast::n_chunks(RD, kChunked<Acc>) == 1) {
-        fast_block1<L, RD, 0>(x, regB, pos);
+    constexpr int NC = fast::n_chunks(RD, CM);
+    static_assert(NC >= 1 && NC <= 3, "at most three chunks per round");
+    if constexpr (NC == 1) {
+        fast_block1<L, RD, 0, CM>(x, regB, pos);
+    } else if constexpr (NC == 2) {
+        if (C == 0)
+            fast_block1<L, RD, 0, CM>(x, regB, pos);
+        else
+            fast_block1<L, RD, 1, CM>(x, regB, pos);
     } else {
         if (C == 0)
-            fast_block1<L, RD, 0>(x, regB, pos);
+            fast_block1<L, RD, 0, CM>(x, regB, pos);
+        else if (C == 1)
+            fast_block1<L, RD, 1, CM>(x, regB, pos);
         else
-            fast_block1<L, RD, 1>(x, regB, pos);
+            fast_block1<L, RD, 2, CM>(x, regB, pos);
     }
 }
 
@@ -349,22 +365,22 @@ __device__ __forceinline__ void fast_block1_chunk(const Acc (&x)[16], Acc *regB,
 // code of blocks 2 and 3): blocks 2 and 3 of the chunk, then block 1 of the
 // next chunk (of this round or the next), which only touches the level-4
 // region that block 2 has finished reading.
-template <int L, int RD, typename Acc>
+template <int L, int RD, int CM, typename Acc>
 __device__ __forceinline__ void fast_round(const Acc (&x)[16], Acc *regA, Acc *regB, Acc *regY, int tid,
                                            int pos) {
-    constexpr int NC = fast::n_chunks(RD, kChunked<Acc>);
+    constexpr int NC = fast::n_chunks(RD, CM);
 #pragma unroll 1
     for (int c = 0; c < NC; ++c) {
-        fast_block2<L, RD>(regB, regA, tid);
+        fast_block2<L, RD, CM>(regB, regA, tid);
         __syncthreads();
-        fast_block3<L, RD>(regA, regY, tid, c);
+        fast_block3<L, RD, CM>(regA, regY, tid, c);
         if (c + 1 < NC)
-            fast_block1_chunk<L, RD>(x, regB, pos, c + 1);
+            fast_block1_chunk<L, RD, CM>(x, regB, pos, c + 1);
         else if constexpr (RD < L)
-            fast_block1<L, RD + 1, 0>(x, regB, pos);
+            fast_block1<L, RD + 1, 0, CM>(x, regB, pos);
         __syncthreads();
     }
-    if constexpr (RD < L) fast_round<L, RD + 1>(x, regA, regB, regY, tid, pos);
+    if constexpr (RD < L) fast_round<L, RD + 1, CM>(x, regA, regB, regY, tid, pos);
 }
 
 // Weight rows in shared memory per tile, row (s, |S_L|, i) holding the
@@ -429,19 +445,19 @@ __device__ __forceinline__ __int128 fast_g_staged64(const long long *w, const lo
     return acc;
 }
 
-template <typename Acc, int L>
+template <typename Acc, int L, int CM = kChunked<Acc>>
 __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long long game, const long long tile) {
     using In = typename TileTraits<Acc>::In;
     using GT = typename GTraits<Acc>::G;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Acc *tileS = reinterpret_cast<Acc *>(smem_raw);  // the tile during the Moebius transform
     Acc *regB = tileS;                                // then one chunk's level-4 states
-    Acc *regA = regB + fast::reg4_elems(L, kChunked<Acc>);  // and one chunk's level-8 states
-    Acc *regY = tileS + fast::regT_elems(L, kChunked<Acc>);  // channels
+    Acc *regA = regB + fast::reg4_elems(L, CM);  // and one chunk's level-8 states
+    Acc *regY = tileS + fast::regT_elems(L, CM);  // channels
     using WT = typename WTraits<Acc>::W;
     // this tile's weight rows: the first 16-byte boundary after the channels
     constexpr size_t kWOff =
-        ((size_t)(fast::regT_elems(L, kChunked<Acc>) + fast::n_chan(L)) * sizeof(Acc) + 15) & ~(size_t)15;
+        ((size_t)(fast::regT_elems(L, CM) + fast::n_chan(L)) * sizeof(Acc) + 15) & ~(size_t)15;
     WT *wst = reinterpret_cast<WT *>(smem_raw + kWOff);
     __shared__ int s_emax;
 
@@ -518,11 +534,11 @@ __device__ __forceinline__ void tile_fast_body(const FastArgs &a, const long lon
     __syncthreads();
     // ---- ranked sums: block 1 of round 0, then the rounds ----
     const int pos = t3 + 16 * t2;
-    fast_block1<L, 0, 0>(x, regB, pos);
+    fast_block1<L, 0, 0, CM>(x, regB, pos);
     // the weight rows are read only after this barrier
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    fast_round<L, 0>(x, regA, regB, regY, tid, pos);
+    fast_round<L, 0, CM>(x, regA, regB, regY, tid, pos);
     // ---- partial scores G(S_L, s, i) of this tile ----
     // partial scores of a game are stored entry-major, [n_g][2^h tiles], so
     // that the combine's lanes (consecutive tiles) read consecutive addresses
@@ -606,7 +622,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks<Acc, L>) fsi_tile
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(base + o));
         }
     }
-    tile_fast_body<Acc, L>(a, a.game0 + blockIdx.y, blockIdx.x);
+    tile_fast_body<Acc, L, kTileChunkMode<Acc>>(a, a.game0 + blockIdx.y, blockIdx.x);
 }
 
 }  // namespace ttfsi
