@@ -284,7 +284,12 @@ tt_fsi_status plan_build_host(Plan &p, int d, int ell, tt_fsi_arith arith, int64
     // fast tile path: shared-memory regions of fast_layout.h
     if (want_fast) {
         if (fast::n_chan(p.ell_eff) != p.n_ch) return TT_FSI_ERR_UNSUPPORTED;  // layouts disagree
-        const bool chunked = arith == TT_FSI_ARITH_EXACT;  // as the kernels' kChunked
+        // the fast launches are sized for chunk mode 1 (the persistent
+        // kernels' layout); the tile launch runs mode 2, which must fit in that
+        static_assert(fast::regT_elems(1, 2) <= fast::regT_elems(1, 1) && fast::regT_elems(2, 2) <= fast::regT_elems(2, 1) &&
+                          fast::regT_elems(3, 2) <= fast::regT_elems(3, 1) && fast::regT_elems(4, 2) <= fast::regT_elems(4, 1),
+                      "three round-2 chunks must not need more shared memory than two");
+        const bool chunked = arith == TT_FSI_ARITH_EXACT;  // as the kernels' kChunked (mode 1)
         p.fast_regA = fast::reg8_elems(p.ell_eff, chunked);
         p.fast_regB = fast::reg4_elems(p.ell_eff, chunked);
         // tile / chunk states and channels, then the tile's weight rows
